@@ -1,0 +1,80 @@
+"""Pins of the oracle minimiser (properties of the variational minimum) and of
+the electron-ion structure factor (Methods, S_ab(q) definition)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.functional import Functional
+from oracle.minimize import lbfgs
+from oracle.sei import sei_shells
+from oracle.cell import structure_factor
+from workloads import fcc_cell, random_cell
+
+
+@pytest.fixture(scope="module")
+def small_min():
+    c = fcc_cell(n=16)
+    F = Functional(c)
+    r = lbfgs(F, tol_F=1e-11, tol_R=1e-8, max_iter=400)
+    return c, F, r
+
+
+def test_minimum_conserves_electrons_and_is_stationary(small_min):
+    c, F, r = small_min
+    assert r.converged
+    assert abs(F.dV * r.rho.sum() - c.n_electrons) < 1e-12 * c.n_electrons
+    assert r.energies["residual"] < 1e-8
+
+
+def test_minimum_is_lower_than_perturbations(small_min):
+    c, F, r = small_min
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        p = r.psi * (1 + 1e-3 * rng.standard_normal(r.psi.shape))
+        assert F.evaluate_psi(p)[0]["total"] > r.energies["total"]
+
+
+def test_minimum_independent_of_optimizer_constants(small_min):
+    c, F0, r0 = small_min
+    F = Functional(c)
+    rng = np.random.default_rng(9)
+    start = np.sqrt(c.n_electrons / c.volume) * (1 + 0.05 * rng.standard_normal((16,) * 3))
+    r = lbfgs(F, psi0=start, m=4, c2=0.5, tol_F=1e-11, tol_R=1e-8, max_iter=600)
+    assert r.converged
+    assert abs(r.energies["total"] - r0.energies["total"]) / c.n_ion < 1e-10
+    assert np.linalg.norm(r.rho - r0.rho) / np.linalg.norm(r0.rho) < 1e-6
+
+
+def test_sei_uniform_is_zero():
+    c = random_cell(21, 8, 1.0, 1.5, 1.0, 16)
+    q, s = sei_shells(np.full((16,) * 3, c.n_electrons / c.volume), c.pos, c.L, c.n_electrons, 40)
+    assert np.max(np.abs(s)) < 1e-12
+    assert np.all(np.diff(q) > 0)
+
+
+def test_sei_of_gaussian_density_closed_form():
+    # n = sum_I Z g_s(r - R_I): n_e(G) = Z exp(-G^2 s^2/2) S(G), so
+    # S_ei(G) = Z exp(-G^2 s^2 / 2) |S(G)|^2 / sqrt(N_e N_i) (shell-averaged)
+    L, n, s, Z = 9.0, 48, 0.5, 1.0
+    pos = np.array([[1.0, 2.0, 3.0], [5.0, 5.5, 1.5], [7.5, 3.0, 7.0]])
+    x = np.arange(n) * L / n
+    X, Y, Zc = np.meshgrid(x, x, x, indexing="ij")
+    rho = np.zeros((n, n, n))
+    for p in pos:
+        d2 = 0
+        for ax, comp in zip((X, Y, Zc), p):
+            d = ax - comp
+            d -= L * np.round(d / L)
+            d2 = d2 + d * d
+        rho += Z * np.exp(-d2 / (2 * s * s)) / (2 * math.pi * s * s) ** 1.5
+    ne = Z * len(pos)
+    q, got = sei_shells(rho, pos, L, ne, 30)
+    S = structure_factor(pos, n, L)
+    m = np.fft.fftfreq(n) * n
+    m2 = (m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2).round().astype(int)
+    G2 = (2 * math.pi / L) ** 2 * m2
+    ref_grid = Z * np.exp(-G2 * s * s / 2) * np.abs(S) ** 2 / math.sqrt(ne * len(pos))
+    vals = np.unique(m2[m2 > 0])[:30]
+    ref = np.array([ref_grid[m2 == v].mean() for v in vals])
+    assert np.allclose(got, ref, atol=1e-9)
