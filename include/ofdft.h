@@ -1,0 +1,216 @@
+/*
+ * ofdft.h -- C-ABI of the GB300 finite-temperature orbital-free DFT library.
+ *
+ * The library evaluates and minimises the free-energy functional of the
+ * paper's orbital-free DFT method on a periodic real-space grid:
+ *
+ *   F[n] = F_s^TF[n;T] + F_s^vW[n] + F_0^NL[n;T]          (Eq. 1 and Eq. 2)
+ *        + E_H[n] + E_loc[n] + E_xc[n] + E_ion
+ *
+ * with the finite-temperature Thomas-Fermi term through Fermi-Dirac integrals
+ * and their inverse, the von Weizsaecker term, the nonlocal kinetic kernel
+ * K(|G|) fixed by the finite-temperature Lindhard response at the mean valence
+ * density (the F_0^NL part of Eq. 2), Perdew-Zunger LDA exchange-correlation
+ * (Methods, "Numerical calculations for OFDFT and KSDFT"), Hartree, a local
+ * pseudopotential through ion structure factors, and the Ewald ion-ion energy.
+ * The density is found by direct minimisation over sqrt(n) at fixed electron
+ * number (the "SCF iterations" of the Methods section, Table 2 caption).
+ *
+ * Units: Hartree atomic units (Ha, bohr).  Cubic cell of side L, n^3 grid.
+ *
+ * Layouts (all device arrays are plain cudaMalloc'd memory owned by the
+ * caller unless stated otherwise):
+ *   real field   double/float [n][n][n], index (ix*n + iy)*n + iz (z fastest),
+ *                point r = (L/n)*(ix, iy, iz).
+ *   half spectrum complex [n][n][n/2+1] (interleaved re, im), index
+ *                (kx*n + ky)*(n/2+1) + kz; integer wave numbers m in FFT order
+ *                (m = k for k < n/2, m = k - n otherwise), G = (2 pi/L) m.
+ *   f~(G) = (1/N) sum_r f(r) exp(-i G.r), N = n^3.
+ * Element type: double for OFDFT_FP64 plans, float for OFDFT_FP32 plans
+ * (FP32 bulk arithmetic with FP64 reductions, FP64 line search).
+ *
+ * Errors: every call returns an ofdft_status; 0 is success.  On failure the
+ * outputs are left unspecified unless the call says otherwise, and
+ * ofdft_last_error() returns a message (thread-local, valid until the next
+ * call on the same thread).  No call aborts the process or faults the GPU on
+ * invalid arguments: arguments are validated on the host first.
+ *
+ * Streams: calls enqueue work on the given stream (0 = legacy default).
+ * Calls that return host results synchronise that stream before returning.
+ * A plan is not thread-safe: one plan, one stream at a time.
+ */
+#ifndef OFDFT_H
+#define OFDFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OFDFT_OK = 0,
+    OFDFT_ERR_INVALID = 1,        /* bad argument (size, pointer, option)          */
+    OFDFT_ERR_CUDA = 2,           /* a CUDA runtime call failed                    */
+    OFDFT_ERR_OOM = 3,            /* device allocation failed                      */
+    OFDFT_ERR_NOT_CONVERGED = 4,  /* minimiser stopped before the tolerances       */
+    OFDFT_ERR_TIMEOUT = 5,        /* a bounded device wait ran out                 */
+    OFDFT_ERR_NAN = 6             /* a non-finite energy or density was produced   */
+} ofdft_status;
+
+typedef enum { OFDFT_FP64 = 0, OFDFT_FP32 = 1 } ofdft_precision;
+
+/* Which terms of F enter (bit mask); OFDFT_TERMS_ALL is the full functional.
+ * Switching terms off gives the paper's ablations, e.g. TF-only. */
+enum {
+    OFDFT_TERM_TF = 1, OFDFT_TERM_VW = 2, OFDFT_TERM_NL = 4, OFDFT_TERM_XC = 8,
+    OFDFT_TERM_HARTREE = 16, OFDFT_TERM_LOC = 32, OFDFT_TERMS_ALL = 63
+};
+
+/* The cell.  Z points to host memory and is copied by ofdft_plan_create. */
+typedef struct {
+    double L;            /* cubic cell side, bohr (> 0)                                */
+    int n;               /* grid points per side: even, 2,3,5-smooth, 8 <= n <= 512    */
+    int n_ion;           /* number of ions (>= 1)                                      */
+    const double* Z;     /* host [n_ion] valence charges (> 0); N_e = sum Z            */
+    double rc;           /* Gaussian smoothing radius of the local ion potential, bohr */
+    double T;            /* electron temperature, Ha (> 0)                             */
+} ofdft_cell;
+
+/* Functional options. */
+typedef struct {
+    int precision;       /* ofdft_precision                                            */
+    int terms;           /* OFDFT_TERM_* mask                                          */
+    double alpha;        /* exponent a of E_NL = int int n^a K n^a (0 < a < 1)         */
+} ofdft_opts;
+
+/* Energies in Ha (per cell) and derived scalars. */
+typedef struct {
+    double F_TF, E_vW, E_NL, E_H, E_loc, E_xc, E_ion;
+    double F_total;      /* sum of the seven terms above                               */
+    double N_e;          /* integral of the density                                    */
+    double mu;           /* chemical potential int v n / N_e, Ha                       */
+    double residual;     /* (int n (v - mu)^2 / N_e)^(1/2), Ha                         */
+} ofdft_energies;
+
+/* Minimiser options (L-BFGS on sqrt(n), strong-Wolfe line search). */
+typedef struct {
+    double tol_F_per_ion; /* |dF|/N_ion below this for 3 consecutive iterations ...   */
+    double tol_residual;  /* ... and residual below this, Ha                           */
+    int m;                /* L-BFGS memory (1..16)                                     */
+    int max_iter;         /* iteration cap                                             */
+    double c1, c2;        /* Wolfe constants (sufficient decrease, curvature)          */
+} ofdft_min_opts;
+
+typedef struct {
+    ofdft_energies e;
+    int iterations;
+    int evaluations;      /* functional evaluations (incl. line-search trials)         */
+    int status;           /* OFDFT_OK or OFDFT_ERR_NOT_CONVERGED                       */
+} ofdft_result;
+
+typedef struct ofdft_plan ofdft_plan;
+
+/* Defaults: FP64, all terms, alpha = 1/2; tol 1e-6 Ha/ion, residual 1e-4 Ha,
+ * m = 8, max_iter = 1000, c1 = 1e-4, c2 = 0.9. */
+void ofdft_default_opts(ofdft_opts* opts);
+void ofdft_default_min_opts(ofdft_min_opts* opts);
+
+const char* ofdft_last_error(void);
+const char* ofdft_version(void);
+
+/*
+ * Create a plan for one cell: validates the cell, allocates every device
+ * workspace the plan needs (FFT spectra, gradient and L-BFGS history, kernel
+ * table K(|G|), reduction scratch) on the current device, and builds the
+ * nonlocal kernel table from the finite-T Lindhard function at the mean density
+ * (the F_0^NL kernel "that depends only on the mean valence electron density",
+ * Results after Eq. 2).  Ion positions are given later by
+ * ofdft_structure_factor.  Enqueued on `stream`, which is synchronised before
+ * return.  *out receives the plan; on error *out is NULL.
+ */
+int ofdft_plan_create(const ofdft_cell* cell, const ofdft_opts* opts, void* stream,
+                      ofdft_plan** out);
+
+/* Release a plan and its device memory.  NULL is accepted; calling it twice on
+ * the same pointer is the caller's error (the pointer is freed by the first). */
+void ofdft_plan_destroy(ofdft_plan* plan);
+
+/* Bytes of device memory held by a plan for this cell and these options,
+ * without allocating (for admission control).  Returns 0 on invalid input. */
+size_t ofdft_plan_bytes(const ofdft_cell* cell, const ofdft_opts* opts);
+
+/*
+ * Ion structure factor S(G) = sum_I exp(-i G.R_I) (the reciprocal-space ion
+ * density n_i(q) of the static structure factor definition, Methods) for the
+ * positions `pos` [n_ion][3] (Cartesian, bohr; wrapped into [0, L)).  `pos` is
+ * host memory when pos_on_device == 0, device memory otherwise.
+ * Also builds, inside the plan, the local pseudopotential
+ * V_loc(G) = (1/Omega) sum_I v~_I(G) exp(-i G.R_I) with
+ * v~(G) = -4 pi Z exp(-G^2 rc^2/4)/G^2, v~(0) = pi Z rc^2, and the Ewald energy.
+ * S_out: device half spectrum (element type of the plan) or NULL to skip it.
+ * Must be called before any energy evaluation.  Synchronises `stream`.
+ */
+int ofdft_structure_factor(ofdft_plan* plan, const double* pos, int pos_on_device,
+                           void* S_out, void* stream);
+
+/*
+ * One functional evaluation at density `rho` (device real field, element
+ * type of the plan; not modified).  Writes the potential v = dF/dn to v_out
+ * (device real field, may be NULL) and the energies to *e_out (host, may be
+ * NULL).  v includes v_vW = -lap(sqrt n)/(2 sqrt n), with sqrt n floored at
+ * 1e-10.  Synchronises `stream` when e_out is not NULL.
+ */
+int ofdft_energy_potential(ofdft_plan* plan, const void* rho, void* v_out,
+                           ofdft_energies* e_out, void* stream);
+
+/*
+ * Minimise F over n = N_e psi^2 / int psi^2 by L-BFGS with a strong-Wolfe line
+ * search.  rho_io: device real field; on entry the initial density (or NULL
+ * contents ignored when start_uniform != 0, which starts from the uniform
+ * density N_e/Omega); on exit the converged density.  Returns
+ * OFDFT_ERR_NOT_CONVERGED (and still writes rho_io and *r) when max_iter is
+ * reached or the line search fails.  Deterministic for a fixed input, plan and
+ * options.  Synchronises `stream`.
+ */
+int ofdft_minimize(ofdft_plan* plan, void* rho_io, int start_uniform,
+                   const ofdft_min_opts* o, ofdft_result* r, void* stream);
+
+/*
+ * Electron-ion static structure factor on |q| shells (Methods, S_ab(q) for one
+ * snapshot): for the k-th distinct nonzero integer m^2 present on the grid
+ * (k = 0 .. n_shells-1, ascending),
+ *   S_ei(q_k) = (1/sqrt(N_e N_i)) < Re[ n_e(G) S*(G) ] >_{|m|^2 = m2_k},
+ * n_e(G) = Omega n~(G), averaged over every G of the shell (full sphere).
+ * rho: device real field.  q_out, s_out: host [n_shells] (q in 1/bohr).
+ * Requires ofdft_structure_factor first.  Synchronises `stream`.
+ */
+int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_out,
+                     double* s_out, void* stream);
+
+/*
+ * Per-kernel launch statistics (tracing).  The paper reports only wall times
+ * (Tables 2 and 3); these counters attribute device time to the library's own
+ * kernels.  Launch counts are always kept.  With timing enabled, every launch
+ * of the plan is bracketed by CUDA events recorded on its launch stream and the
+ * device time is accumulated per kernel name; this adds host work per launch
+ * but no device synchronisation.  ofdft_profile_enable resets the counters.
+ * ofdft_profile_read synchronises the plan's outstanding events, fills up to
+ * `max` entries of `out` (host) and sets *count to the number of kernels seen.
+ */
+typedef struct {
+    char name[32];
+    long long launches;
+    double total_ms;      /* device time, 0 unless timing was enabled */
+    double bytes;         /* algorithmic DRAM bytes of those launches (inputs read
+                             once, outputs written once)                       */
+} ofdft_kernel_stat;
+
+int ofdft_profile_enable(ofdft_plan* plan, int timing);
+int ofdft_profile_read(ofdft_plan* plan, ofdft_kernel_stat* out, int max, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OFDFT_H */

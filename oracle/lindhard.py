@@ -42,11 +42,14 @@ def _occ(k, mu0, T):
     return 1.0 / (1.0 + math.exp(u))
 
 
-def chi0(q: float, mu0: float, T: float) -> float:
-    """Static finite-T Lindhard function (negative), q > 0.
+def _excess_integral(q: float, mu0: float, T: float) -> float:
+    """I = int_0^inf k f(k) [ln|(2k+q)/(2k-q)| - 4k/q] dk.
 
-    The k-integral is split around the Fermi edge sqrt(2 mu0) and at the
-    logarithmic singularity q/2; on a piece that ends at q/2 the singular factor
+    The leading large-q term 4k/q integrates to (4/q) pi^2 nbar exactly, so
+    chi0 = -(4 nbar/q^2) (1 + eps) with eps = I q / (4 pi^2 nbar).  Working with
+    I avoids subtracting two numbers of size q^2/(4 nbar) when the kernel is
+    formed.  The integral is split around the Fermi edge sqrt(2 mu0) and at the
+    logarithmic singularity q/2; on a piece that ends at q/2 the factor
     ln|k - q/2| is integrated with QUADPACK's algebraic-logarithmic weight.
     """
     kmax = math.sqrt(2.0 * max(mu0 + 45.0 * T, 45.0 * T))
@@ -63,20 +66,45 @@ def chi0(q: float, mu0: float, T: float) -> float:
         brk.add(h)
     pts = sorted(brk)
     g = lambda k: k * _occ(k, mu0, T)
+
+    def excess(k):
+        # ln|(1+x)/(1-x)| - 2x with x = 2k/q, written as 2(atanh x - x) below 1
+        x = 2.0 * k / q
+        if x < 1.0:
+            return 2.0 * (math.atanh(x) - x)
+        return math.log((x + 1.0) / (x - 1.0)) - 2.0 * x
+
     total = 0.0
     for a, b in zip(pts[:-1], pts[1:]):
         if b <= a:
             continue
         if a == h or b == h:
-            # k f(k) [ln(2k + q) - ln 2 - ln|k - q/2|]
-            reg = integrate.quad(lambda k: g(k) * (math.log(2.0 * k + q) - math.log(2.0)), a, b, **opts)[0]
+            # k f(k) [ln(2k + q) - ln 2 - 4k/q - ln|k - q/2|]
+            reg = integrate.quad(lambda k: g(k) * (math.log(2.0 * k + q) - math.log(2.0) - 4.0 * k / q),
+                                 a, b, **opts)[0]
             w = "alg-loga" if a == h else "alg-logb"
             sing = integrate.quad(g, a, b, weight=w, wvar=(0.0, 0.0), **opts)[0]
             total += reg - sing
         else:
-            total += integrate.quad(lambda k: g(k) * math.log(abs((2.0 * k + q) / (2.0 * k - q))),
-                                    a, b, **opts)[0]
-    return -total / (PI2 * q)
+            total += integrate.quad(lambda k: g(k) * excess(k), a, b, **opts)[0]
+    return total
+
+
+def chi0(q: float, mu0: float, T: float, nbar: float | None = None) -> float:
+    """Static finite-T Lindhard function (negative), q > 0.  nbar is the
+    ideal-gas density at (mu0, T); computed from the Fermi-Dirac integral when
+    not given."""
+    if nbar is None:
+        nbar = float(SQRT2 / PI2 * T ** 1.5 * fd_integral(0.5, np.array([mu0 / T]))[0])
+    eps = _excess_integral(q, mu0, T) * q / (4.0 * PI2 * nbar)
+    return -4.0 * nbar / (q * q) * (1.0 + eps)
+
+
+def response_excess(q: float, mu0: float, T: float, nbar: float) -> float:
+    """-1/chi0(q) - q^2/(4 nbar) = -(q^2/(4 nbar)) eps/(1 + eps), formed
+    without cancellation."""
+    eps = _excess_integral(q, mu0, T) * q / (4.0 * PI2 * nbar)
+    return -q * q / (4.0 * nbar) * eps / (1.0 + eps)
 
 
 def chi0_zero_T(q: float, kf: float) -> float:
@@ -102,8 +130,7 @@ def kernel_value(q: float, nbar: float, T: float, mu0: float, dmu: float,
     """K(q) from the response condition; K(0) = 0."""
     if q == 0.0:
         return 0.0
-    resp = -1.0 / chi0(q, mu0, T)
-    return (resp - dmu - q * q / (4.0 * nbar)) / (2.0 * alpha * alpha * nbar ** (2 * alpha - 2))
+    return (response_excess(q, mu0, T, nbar) - dmu) / (2.0 * alpha * alpha * nbar ** (2 * alpha - 2))
 
 
 def kernel_table(m2_values, L: float, nbar: float, T: float, alpha: float = ALPHA) -> np.ndarray:

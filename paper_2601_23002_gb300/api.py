@@ -1,0 +1,143 @@
+"""Thin Python binding over the C-ABI (argument marshalling only).
+
+Every step of the computation runs in the CUDA library; PyTorch provides the
+device memory and the stream.  Functions raise OfdftError on a non-zero
+status (minimize returns the partial result with status NOT_CONVERGED).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as C
+
+
+class OfdftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ofdft status {C.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(rc: int):
+    if rc != C.OFDFT_OK:
+        raise OfdftError(rc, C.last_error())
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Plan:
+    """One cell: L (bohr), n, Z[n_ion], rc (bohr), T (Ha)."""
+
+    def __init__(self, L: float, n: int, Z, T: float, rc: float = 1.0, precision: str = "fp64",
+                 terms: int = C.TERMS_ALL, alpha: float = 0.5, stream=None):
+        self.lib = C.load()
+        self._Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64))
+        self.cell = C.Cell(float(L), int(n), int(self._Z.size),
+                           self._Z.ctypes.data_as(C.c_double_p), float(rc), float(T))
+        self.opts = C.Opts(C.OFDFT_FP32 if precision == "fp32" else C.OFDFT_FP64, int(terms), float(alpha))
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        self.n = int(n)
+        self.stream = stream
+        self._p = ctypes.c_void_p()
+        _check(self.lib.ofdft_plan_create(ctypes.byref(self.cell), ctypes.byref(self.opts),
+                                          _stream_ptr(stream), ctypes.byref(self._p)))
+
+    @staticmethod
+    def plan_bytes(L, n, Z, T, rc=1.0, precision="fp64", terms=C.TERMS_ALL, alpha=0.5) -> int:
+        lib = C.load()
+        Zc = np.ascontiguousarray(np.asarray(Z, dtype=np.float64))
+        cell = C.Cell(float(L), int(n), int(Zc.size), Zc.ctypes.data_as(C.c_double_p), float(rc), float(T))
+        opts = C.Opts(C.OFDFT_FP32 if precision == "fp32" else C.OFDFT_FP64, int(terms), float(alpha))
+        return int(lib.ofdft_plan_bytes(ctypes.byref(cell), ctypes.byref(opts)))
+
+    def close(self):
+        if self._p:
+            self.lib.ofdft_plan_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _field(self, t: torch.Tensor, name: str):
+        n = self.n
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == n ** 3):
+            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor with {n}^3 elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def structure_factor(self, pos, S_out: torch.Tensor | None = None):
+        if isinstance(pos, torch.Tensor) and pos.is_cuda:
+            p = pos.contiguous().to(torch.float64)
+            self._pos_keep = p
+            ptr, dev = ctypes.c_void_p(p.data_ptr()), 1
+        else:
+            a = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
+            self._pos_keep = a
+            ptr, dev = ctypes.c_void_p(a.ctypes.data), 0
+        sptr = None
+        if S_out is not None:
+            nh = self.n // 2 + 1
+            want = torch.complex64 if self.dtype == torch.float32 else torch.complex128
+            if not (S_out.is_cuda and S_out.dtype == want and S_out.is_contiguous()
+                    and S_out.numel() == self.n * self.n * nh):
+                raise ValueError("S_out must be a contiguous CUDA complex tensor [n, n, n/2+1]")
+            sptr = ctypes.c_void_p(S_out.data_ptr())
+        _check(self.lib.ofdft_structure_factor(self._p, ptr, dev, sptr, _stream_ptr(self.stream)))
+
+    def energy_potential(self, rho: torch.Tensor, v_out: torch.Tensor | None = None) -> dict:
+        e = C.Energies()
+        vp = self._field(v_out, "v_out") if v_out is not None else None
+        _check(self.lib.ofdft_energy_potential(self._p, self._field(rho, "rho"), vp, ctypes.byref(e),
+                                               _stream_ptr(self.stream)))
+        return e.as_dict()
+
+    def minimize(self, rho: torch.Tensor, start_uniform: bool = True, tol_F_per_ion: float = 1e-6,
+                 tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000, c1: float = 1e-4,
+                 c2: float = 0.9, raise_on_fail: bool = False) -> dict:
+        o = C.MinOpts(tol_F_per_ion, tol_residual, m, max_iter, c1, c2)
+        r = C.Result()
+        rc = self.lib.ofdft_minimize(self._p, self._field(rho, "rho"), int(bool(start_uniform)),
+                                     ctypes.byref(o), ctypes.byref(r), _stream_ptr(self.stream))
+        if rc not in (C.OFDFT_OK, C.OFDFT_ERR_NOT_CONVERGED) or (raise_on_fail and rc):
+            _check(rc)
+        out = r.e.as_dict()
+        out.update(iterations=r.iterations, evaluations=r.evaluations, status=r.status,
+                   converged=r.status == C.OFDFT_OK)
+        return out
+
+    def profile_enable(self, timing: bool = True):
+        """Reset the per-kernel counters; with timing, bracket launches by events."""
+        _check(self.lib.ofdft_profile_enable(self._p, int(bool(timing))))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms, algorithmic bytes)} since the last enable."""
+        cnt = ctypes.c_int(0)
+        _check(self.lib.ofdft_profile_read(self._p, None, 0, ctypes.byref(cnt)))
+        arr = (C.KernelStat * max(1, cnt.value))()
+        _check(self.lib.ofdft_profile_read(self._p, arr, cnt.value, ctypes.byref(cnt)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms), float(arr[i].bytes))
+                for i in range(cnt.value)}
+
+    def sei_shells(self, rho: torch.Tensor, n_shells: int = 200):
+        q = np.zeros(n_shells)
+        s = np.zeros(n_shells)
+        _check(self.lib.ofdft_sei_shells(self._p, self._field(rho, "rho"), int(n_shells),
+                                         q.ctypes.data_as(C.c_double_p), s.ctypes.data_as(C.c_double_p),
+                                         _stream_ptr(self.stream)))
+        return q, s
+
+
+def plan_for_cell(cell, precision="fp64", terms=C.TERMS_ALL, alpha=0.5, stream=None) -> Plan:
+    """Plan + structure factor for a workloads.Cell (or any object with
+    L, n, Z, pos, rc, T)."""
+    p = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=precision, terms=terms, alpha=alpha,
+             stream=stream)
+    p.structure_factor(cell.pos)
+    return p

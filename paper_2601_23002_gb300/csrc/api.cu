@@ -1,0 +1,186 @@
+// C-ABI entry points (include/ofdft.h): argument validation, plan lifetime,
+// dispatch to the FP32 or FP64 engine.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "engine.h"
+
+namespace ofdft {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+// n = product of radices from {16, 12, 10, 9, 8, 6, 5, 4, 3, 2}, fewest passes.
+bool factor_radices(int n, int* radix, int* npass) {
+  static const int cand[] = {16, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  if (n == 1) { *npass = 1; radix[0] = 1; return false; }
+  for (int passes = 1; passes <= 8; ++passes) {
+    // depth-first search for a factorisation with exactly `passes` factors
+    int fac[8];
+    bool found = false;
+    auto dfs = [&](auto&& self, int rem, int depth) -> void {
+      if (found) return;
+      if (depth == passes) { if (rem == 1) found = true; return; }
+      for (int c : cand) {
+        if (rem % c == 0) {
+          fac[depth] = c;
+          self(self, rem / c, depth + 1);
+          if (found) return;
+        }
+      }
+    };
+    dfs(dfs, n, 0);
+    if (found) {
+      *npass = passes;
+      for (int i = 0; i < passes; ++i) radix[i] = fac[i];
+      return true;
+    }
+  }
+  return false;
+}
+
+}  // namespace ofdft
+
+using namespace ofdft;
+
+struct ofdft_plan {
+  IEngine* eng;
+  int precision;
+  int device;
+};
+
+static bool smooth235(int k) {
+  for (int p : {2, 3, 5})
+    while (k % p == 0) k /= p;
+  return k == 1;
+}
+
+static int validate(const ofdft_cell* c, const ofdft_opts* o) {
+  if (!c || !o) { set_error("cell and opts must not be NULL"); return OFDFT_ERR_INVALID; }
+  if (!(c->L > 0) || !std::isfinite(c->L)) { set_error("L must be positive"); return OFDFT_ERR_INVALID; }
+  if (c->n < 8 || c->n > 512 || c->n % 2 || !smooth235(c->n)) {
+    set_error("n must be even, 2,3,5-smooth and in [8, 512]");
+    return OFDFT_ERR_INVALID;
+  }
+  int rad[8], np;
+  if (!factor_radices(c->n, rad, &np) || !factor_radices(c->n / 2, rad, &np)) {
+    set_error("n has no supported radix factorisation");
+    return OFDFT_ERR_INVALID;
+  }
+  if (c->n_ion < 1 || !c->Z) { set_error("need n_ion >= 1 and Z"); return OFDFT_ERR_INVALID; }
+  for (int i = 0; i < c->n_ion; ++i)
+    if (!(c->Z[i] > 0) || !std::isfinite(c->Z[i])) { set_error("every Z must be positive"); return OFDFT_ERR_INVALID; }
+  if (!(c->rc > 0)) { set_error("rc must be positive"); return OFDFT_ERR_INVALID; }
+  if (!(c->T > 0) || !std::isfinite(c->T)) { set_error("T must be positive"); return OFDFT_ERR_INVALID; }
+  if (o->precision != OFDFT_FP64 && o->precision != OFDFT_FP32) { set_error("bad precision"); return OFDFT_ERR_INVALID; }
+  if (o->terms < 0 || o->terms > OFDFT_TERMS_ALL) { set_error("bad terms mask"); return OFDFT_ERR_INVALID; }
+  if (!(o->alpha > 0 && o->alpha < 1)) { set_error("alpha must be in (0, 1)"); return OFDFT_ERR_INVALID; }
+  return OFDFT_OK;
+}
+
+static CellSpec spec_of(const ofdft_cell* c, const ofdft_opts* o) {
+  CellSpec s;
+  s.L = c->L; s.n = c->n; s.Z.assign(c->Z, c->Z + c->n_ion); s.rc = c->rc; s.T = c->T;
+  s.terms = o->terms; s.alpha = o->alpha;
+  return s;
+}
+
+extern "C" {
+
+void ofdft_default_opts(ofdft_opts* o) {
+  if (!o) return;
+  o->precision = OFDFT_FP64;
+  o->terms = OFDFT_TERMS_ALL;
+  o->alpha = 0.5;
+}
+
+void ofdft_default_min_opts(ofdft_min_opts* o) {
+  if (!o) return;
+  o->tol_F_per_ion = 1e-6;
+  o->tol_residual = 1e-4;
+  o->m = 8;
+  o->max_iter = 1000;
+  o->c1 = 1e-4;
+  o->c2 = 0.9;
+}
+
+const char* ofdft_last_error(void) { return g_err.c_str(); }
+const char* ofdft_version(void) { return "ofdft-gb300 0.1 (sm_103a)"; }
+
+size_t ofdft_plan_bytes(const ofdft_cell* cell, const ofdft_opts* opts) {
+  if (validate(cell, opts)) return 0;
+  return engine_bytes(spec_of(cell, opts), opts->precision, 8);
+}
+
+int ofdft_plan_create(const ofdft_cell* cell, const ofdft_opts* opts, void* stream, ofdft_plan** out) {
+  if (!out) { set_error("out must not be NULL"); return OFDFT_ERR_INVALID; }
+  *out = nullptr;
+  int rc = validate(cell, opts);
+  if (rc) return rc;
+  ofdft_plan* p = new (std::nothrow) ofdft_plan;
+  if (!p) { set_error("host allocation failed"); return OFDFT_ERR_OOM; }
+  p->precision = opts->precision;
+  cudaGetDevice(&p->device);
+  CellSpec s = spec_of(cell, opts);
+  p->eng = opts->precision == OFDFT_FP32 ? make_engine_f32(s, 8) : make_engine_f64(s, 8);
+  rc = p->eng->create(stream);
+  if (rc) {
+    std::string keep = ofdft_last_error();
+    delete p->eng;
+    delete p;
+    set_error(keep);
+    return rc;
+  }
+  *out = p;
+  return OFDFT_OK;
+}
+
+void ofdft_plan_destroy(ofdft_plan* plan) {
+  if (!plan) return;
+  delete plan->eng;
+  delete plan;
+}
+
+int ofdft_structure_factor(ofdft_plan* plan, const double* pos, int pos_on_device, void* S_out, void* stream) {
+  if (!plan || !pos) { set_error("plan and pos must not be NULL"); return OFDFT_ERR_INVALID; }
+  return plan->eng->set_ions(pos, pos_on_device, S_out, stream);
+}
+
+int ofdft_energy_potential(ofdft_plan* plan, const void* rho, void* v_out, ofdft_energies* e_out, void* stream) {
+  if (!plan || !rho) { set_error("plan and rho must not be NULL"); return OFDFT_ERR_INVALID; }
+  return plan->eng->energy_potential(rho, v_out, e_out, stream);
+}
+
+int ofdft_minimize(ofdft_plan* plan, void* rho_io, int start_uniform, const ofdft_min_opts* o, ofdft_result* r,
+                   void* stream) {
+  if (!plan || !rho_io) { set_error("plan and rho_io must not be NULL"); return OFDFT_ERR_INVALID; }
+  ofdft_min_opts d;
+  ofdft_default_min_opts(&d);
+  const ofdft_min_opts& oo = o ? *o : d;
+  if (oo.m < 1 || oo.m > 8 || oo.max_iter < 1 || !(oo.c1 > 0) || !(oo.c2 > oo.c1) || !(oo.c2 < 1)) {
+    set_error("bad minimiser options (m in 1..8, max_iter >= 1, 0 < c1 < c2 < 1)");
+    return OFDFT_ERR_INVALID;
+  }
+  return plan->eng->minimize(rho_io, start_uniform, oo, r, stream);
+}
+
+int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_out, double* s_out, void* stream) {
+  if (!plan || !rho || !q_out || !s_out) { set_error("NULL argument"); return OFDFT_ERR_INVALID; }
+  return plan->eng->sei_shells(rho, n_shells, q_out, s_out, stream);
+}
+
+int ofdft_profile_enable(ofdft_plan* plan, int timing) {
+  if (!plan) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
+  return plan->eng->profile_enable(timing);
+}
+
+int ofdft_profile_read(ofdft_plan* plan, ofdft_kernel_stat* out, int max, int* count) {
+  if (!plan || max < 0) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
+  return plan->eng->profile_read(out, max, count);
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// Internal interface between the C-ABI layer (api.cu) and the per-precision
+// engines (engine_f32.cu, engine_f64.cu).  Not part of the public header.
+#pragma once
+#include <stddef.h>
+#include <string>
+#include <vector>
+
+#include "../../include/ofdft.h"
+
+namespace ofdft {
+
+struct CellSpec {
+  double L;
+  int n;
+  std::vector<double> Z;
+  double rc;
+  double T;
+  int terms;
+  double alpha;
+};
+
+class IEngine {
+ public:
+  virtual ~IEngine() {}
+  virtual int create(void* stream) = 0;
+  virtual int set_ions(const double* pos, int on_device, void* S_out, void* stream) = 0;
+  virtual int energy_potential(const void* rho, void* v_out, ofdft_energies* e, void* stream) = 0;
+  virtual int minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o, ofdft_result* r,
+                       void* stream) = 0;
+  virtual int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream) = 0;
+  virtual size_t bytes() const = 0;
+  virtual int profile_enable(int timing) = 0;
+  virtual int profile_read(ofdft_kernel_stat* out, int max, int* count) = 0;
+};
+
+IEngine* make_engine_f32(const CellSpec& c, int m_max);
+IEngine* make_engine_f64(const CellSpec& c, int m_max);
+size_t engine_bytes(const CellSpec& c, int precision, int m_max);
+
+// thread-local error message shared by all layers
+void set_error(const std::string& msg);
+
+// 1-D FFT factorisation into supported radices; false if n is not supported
+bool factor_radices(int n, int* radix, int* npass);
+
+}  // namespace ofdft

@@ -1,0 +1,711 @@
+// Per-precision engine: device buffers of one plan, the evaluation pipeline,
+// setup, S_ei, and the L-BFGS driver.  Included by engine_f32.cu / engine_f64.cu.
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "profiler.h"
+#include "fft.cuh"
+#include "passes.cuh"
+#include "setup.cuh"
+#include "vecops.cuh"
+
+namespace ofdft {
+
+#define OFDFT_CK(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_error(std::string("CUDA error: ") + cudaGetErrorString(e_) + " at " + #call); \
+      return e_ == cudaErrorMemoryAllocation ? OFDFT_ERR_OOM : OFDFT_ERR_CUDA;          \
+    }                                                                                   \
+  } while (0)
+
+#define OFDFT_LAUNCH_CK()                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) {                                                            \
+      set_error(std::string("CUDA launch error: ") + cudaGetErrorString(e_));           \
+      return OFDFT_ERR_CUDA;                                                            \
+    }                                                                                   \
+  } while (0)
+
+#define OFDFT_RUN(name, st, bytes, ...)  \
+  do {                            \
+    prof.begin(name, st, (double)(bytes)); \
+    __VA_ARGS__;                  \
+    prof.end(st);                 \
+    OFDFT_LAUNCH_CK();            \
+  } while (0)
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void k_convert_table(const double* __restrict__ a, T* __restrict__ b, int cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) b[i] = (T)a[i];
+}
+constexpr int kMaxMem = 16;
+
+// ring slot of the i-th oldest history pair
+struct Ring {
+  int head = 0, count = 0, m = 8;
+  int slot(int i) const { return (head + i) % m; }   // i = 0 oldest
+  int push() {                                      // returns slot for the new pair
+    int s;
+    if (count < m) { s = (head + count) % m; ++count; }
+    else { s = head; head = (head + 1) % m; }
+    return s;
+  }
+  void clear() { head = 0; count = 0; }
+};
+
+template <typename T>
+class Engine : public IEngine {
+ public:
+  using C = cplx<T>;
+  CellSpec cs;
+  int n = 0, nh = 0, h = 0;
+  size_t N = 0, NH = 0;
+  double L = 0, Omega = 0, dV = 0, Ne = 0, nbar = 0, Te = 0;
+  int m_max = 8;
+  FftPlan1 pn{}, ph{};
+  // launch geometry
+  int zR = 0, zP = 0, yJ = 0, xJ = 0;
+  size_t smem_zf = 0, smem_zi = 0, smem_y = 0, smem_x = 0;
+  int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0;
+  // device memory
+  std::vector<void*> allocs;
+  size_t nbytes = 0;
+  C *tw_n = nullptr, *tw_h = nullptr;
+  double* Kd = nullptr;
+  T* Kt = nullptr;
+  C* vloc = nullptr;
+  C* Sg = nullptr;
+  C* spec[3] = {nullptr, nullptr, nullptr};
+  T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
+  T* Sh[kMaxMem] = {};
+  T* Yh[kMaxMem] = {};
+  double* partials = nullptr;
+  size_t partials_cap = 0;
+  double* res_d = nullptr;
+  double* res_h = nullptr;     // pinned
+  double* pos_d = nullptr;
+  double* Z_d = nullptr;
+  double2* phases = nullptr;
+  double E_ion = 0;
+  bool ions_set = false;
+  double g2cut_loc = 0;
+  size_t n_vloc = 0;         // half-spectrum entries with |G|^2 <= g2cut_loc
+  double mean_params[4] = {0, 0, 0, 0};
+  Profiler prof;
+
+  explicit Engine(const CellSpec& c, int mmax) : cs(c), m_max(mmax) {}
+  ~Engine() override {
+    for (void* p : allocs) cudaFree(p);
+    if (res_h) cudaFreeHost(res_h);
+  }
+  size_t bytes() const override { return nbytes; }
+  int profile_enable(int timing) override { prof.reset(timing != 0); return OFDFT_OK; }
+  int profile_read(ofdft_kernel_stat* out, int max, int* count) override {
+    const auto& st = prof.stats();
+    int i = 0;
+    for (const auto& kv : st) {
+      if (out && i < max) {
+        std::memset(out[i].name, 0, sizeof(out[i].name));
+        std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+        out[i].launches = kv.second.launches;
+        out[i].total_ms = kv.second.ms;
+        out[i].bytes = kv.second.bytes;
+      }
+      ++i;
+    }
+    if (count) *count = i;
+    return OFDFT_OK;
+  }
+
+  template <typename P> int alloc(P** p, size_t count) {
+    void* q = nullptr;
+    const size_t b = count * sizeof(P);
+    cudaError_t e = cudaMalloc(&q, b > 0 ? b : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("device allocation of ") + std::to_string(b) + " bytes failed: " +
+                cudaGetErrorString(e));
+      return OFDFT_ERR_OOM;
+    }
+    allocs.push_back(q);
+    nbytes += b;
+    *p = reinterpret_cast<P*>(q);
+    return OFDFT_OK;
+  }
+
+  bool use_n() const { return (cs.terms & (OFDFT_TERM_HARTREE | OFDFT_TERM_LOC)) != 0; }
+  bool use_na() const { return (cs.terms & OFDFT_TERM_NL) != 0; }
+  bool use_psi() const { return (cs.terms & OFDFT_TERM_VW) != 0; }
+
+  Spectra<T> spectra() const {
+    Spectra<T> s{};
+    s.nact = 0;
+    const bool on[3] = {use_n(), use_na(), use_psi()};
+    for (int f = 0; f < 3; ++f) {
+      s.s[f] = on[f] ? spec[f] : nullptr;
+      if (on[f]) s.idx[s.nact++] = f;
+    }
+    return s;
+  }
+
+  static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+  void geometry() {
+    n = cs.n; h = n / 2; nh = h + 1;
+    N = (size_t)n * n * n;
+    NH = (size_t)n * n * nh;
+    L = cs.L; Omega = L * L * L; dV = Omega / (double)N;
+    Ne = 0; for (double z : cs.Z) Ne += z;
+    nbar = Ne / Omega; Te = cs.T;
+    zR = std::max(1, std::min(32, 2048 / h));
+    zP = nh | 1;                                  // odd row pitch >= h + 1
+    yJ = sizeof(T) == 4 ? 16 : 8;
+    xJ = yJ;
+    smem_zf = align16((size_t)zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
+    smem_zi = align16((size_t)3 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
+    smem_y = 2 * (size_t)n * yJ * sizeof(C);
+    smem_x = smem_y;
+    grid_z = (int)(((size_t)n * n + zR - 1) / zR);
+    grid_y1 = n * ((nh + yJ - 1) / yJ);
+    grid_x = (int)(((size_t)n * nh + xJ - 1) / xJ);
+    grid_vec = (int)std::min<size_t>(1024, (N + kThreads - 1) / kThreads);
+  }
+
+  size_t plan_bytes_estimate() {
+    geometry();
+    size_t b = 0;
+    b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
+    b += (4 + 2 * (size_t)m_max) * N * sizeof(T);            // psi d g gp + history
+    b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
+    b += (size_t)(n + h) * sizeof(C);
+    return b;
+  }
+
+  int create(void* stream_) override {
+    cudaStream_t st = (cudaStream_t)stream_;
+    geometry();
+    if (!factor_radices(n, pn.radix, &pn.npass) || !factor_radices(h, ph.radix, &ph.npass)) {
+      set_error("grid size not supported by the FFT radices");
+      return OFDFT_ERR_INVALID;
+    }
+    pn.n = n; ph.n = h;
+    int rc;
+    // twiddles
+    std::vector<C> twn(n), twh(h);
+    for (int t = 0; t < n; ++t) {
+      long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)n;
+      twn[t] = mk<T>((T)cosl(a), (T)sinl(a));
+    }
+    for (int t = 0; t < h; ++t) {
+      long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)h;
+      twh[t] = mk<T>((T)cosl(a), (T)sinl(a));
+    }
+    if ((rc = alloc(&tw_n, n))) return rc;
+    if ((rc = alloc(&tw_h, h))) return rc;
+    OFDFT_CK(cudaMemcpyAsync(tw_n, twn.data(), n * sizeof(C), cudaMemcpyHostToDevice, st));
+    OFDFT_CK(cudaMemcpyAsync(tw_h, twh.data(), h * sizeof(C), cudaMemcpyHostToDevice, st));
+    // buffers
+    for (int f = 0; f < 3; ++f)
+      if ((rc = alloc(&spec[f], NH))) return rc;
+    if ((rc = alloc(&vloc, NH))) return rc;
+    if ((rc = alloc(&Sg, NH))) return rc;
+    if ((rc = alloc(&psi, N))) return rc;
+    if ((rc = alloc(&d, N))) return rc;
+    if ((rc = alloc(&g, N))) return rc;
+    if ((rc = alloc(&gp, N))) return rc;
+    for (int i = 0; i < m_max; ++i) {
+      if ((rc = alloc(&Sh[i], N))) return rc;
+      if ((rc = alloc(&Yh[i], N))) return rc;
+    }
+    const int nm2 = 3 * h * h + 1;
+    if ((rc = alloc(&Kd, nm2))) return rc;
+    if ((rc = alloc(&Kt, nm2))) return rc;
+    // eval uses [0, 4 grid_x) for G-space partials and [4 grid_x, 4 grid_x + 8 grid_z) for the epilogue
+    partials_cap = std::max<size_t>({(size_t)grid_x * 4 + (size_t)grid_z * 8, (size_t)grid_vec * kMaxV * kMaxW,
+                                     (size_t)n * n, (size_t)4096});
+    if ((rc = alloc(&partials, partials_cap))) return rc;
+    if ((rc = alloc(&res_d, 64))) return rc;
+    OFDFT_CK(cudaMallocHost(&res_h, 64 * sizeof(double)));
+    if ((rc = alloc(&pos_d, (size_t)cs.Z.size() * 3))) return rc;
+    if ((rc = alloc(&Z_d, cs.Z.size()))) return rc;
+    if ((rc = alloc(&phases, (size_t)cs.Z.size() * 3 * n))) return rc;
+    OFDFT_CK(cudaMemcpyAsync(Z_d, cs.Z.data(), cs.Z.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // shared-memory limits
+    OFDFT_CK(cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_zf));
+    OFDFT_CK(cudaFuncSetAttribute(k_zinv_epi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_zi));
+    OFDFT_CK(cudaFuncSetAttribute(k_ypass<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
+    OFDFT_CK(cudaFuncSetAttribute(k_ypass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
+    OFDFT_CK(cudaFuncSetAttribute(k_xgspace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
+    OFDFT_CK(cudaFuncSetAttribute(k_xpass<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
+    // mean-density ideal gas: eta0, mu0, dmu0/dn
+    const double y = 9.8696044010893586188 * nbar / (1.4142135623730950488 * pow(Te, 1.5));
+    OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, 32, 0, st>>>(y, Te, res_d));
+    OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OFDFT_CK(cudaStreamSynchronize(st));
+    std::memcpy(mean_params, res_h, 4 * sizeof(double));
+    if (use_na()) {
+      KernArgs ka{L, nbar, Te, mean_params[1], mean_params[2], cs.alpha, nm2};
+      OFDFT_RUN("k_kernel_table", st, (double)nm2 * 8, k_kernel_table<<<(nm2 + 127) / 128, 128, 0, st>>>(ka, Kd));
+    } else {
+      OFDFT_CK(cudaMemsetAsync(Kd, 0, nm2 * sizeof(double), st));
+    }
+    OFDFT_RUN("k_convert_table", st, (double)nm2 * (8 + sizeof(T)), k_convert_table<T><<<(nm2 + 255) / 256, 256, 0, st>>>(Kd, Kt, nm2));
+    g2cut_loc = 156.0 / (cs.rc * cs.rc);
+    {
+      const double tp2 = (2.0 * kPi / L) * (2.0 * kPi / L);
+      n_vloc = 0;
+      for (int kx = 0; kx < n; ++kx)
+        for (int ky = 0; ky < n; ++ky) {
+          const int mx = kx <= h - 1 ? kx : kx - n, my = ky <= h - 1 ? ky : ky - n;
+          for (int kz = 0; kz < nh; ++kz)
+            if (tp2 * (double)(mx * mx + my * my + kz * kz) <= g2cut_loc) ++n_vloc;
+        }
+    }
+    OFDFT_CK(cudaStreamSynchronize(st));
+    return OFDFT_OK;
+  }
+
+  // Sum columns of partials[rows][cols] into res_d[off ...] (fixed order).
+  int sum_partials(int rows, int cols, int off, cudaStream_t st) {
+    OFDFT_RUN("k_sum_columns", st, (double)rows * cols * 8, k_sum_columns<<<(cols + 127) / 128, 128, 0, st>>>(partials, rows, cols, res_d + off));
+    return OFDFT_OK;
+  }
+
+  int set_ions(const double* pos, int on_device, void* S_out, void* stream_) override {
+    cudaStream_t st = (cudaStream_t)stream_;
+    const int nion = (int)cs.Z.size();
+    OFDFT_CK(cudaMemcpyAsync(pos_d, pos, (size_t)nion * 3 * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    const int tot = nion * 3 * n;
+    OFDFT_RUN("k_phases", st, (double)tot * 16, k_phases<<<std::min(4096, (tot + 255) / 256), 256, 0, st>>>(pos_d, nion, n, L, phases));
+    // Ewald splitting: reciprocal weights exp(-G^2/(4 eta^2)) below 1e-17 at g2max
+    const double gnyq = kPi * n / L;
+    const double g2max = std::min(g2cut_loc, gnyq * gnyq);
+    const double eta = std::sqrt(g2max / (4.0 * 39.0));
+    const int full = S_out != nullptr;
+    // rows are also kept out to |m|^2 = 600 for the S_ei shells
+    const double g2rows = std::max(g2max, (2.0 * kPi / L) * (2.0 * kPi / L) * 600.0);
+    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<n * n, 128, 0, st>>>(phases, Z_d, nion, n, L, cs.rc, eta, g2rows, full, Sg, vloc, partials));
+    int rc;
+    if ((rc = sum_partials(n * n, 1, 0, st))) return rc;
+    const double rcut = 6.3 / eta;
+    const int nimg = (int)std::ceil(rcut / L) + 1;
+    const long npair = (long)nion * nion;
+    const int gb = (int)std::min<long>(2048, (npair + 255) / 256);
+    OFDFT_RUN("k_ewald_real", st, (double)nion * 32, k_ewald_real<<<gb, 256, 0, st>>>(pos_d, Z_d, nion, L, eta, rcut, nimg, partials));
+    if ((rc = sum_partials(gb, 1, 1, st))) return rc;
+    OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OFDFT_CK(cudaStreamSynchronize(st));
+    double zz = 0;
+    for (double z : cs.Z) zz += z * z;
+    E_ion = res_h[0] + res_h[1] - eta / std::sqrt(kPi) * zz - kPi * Ne * Ne / (2.0 * Omega * eta * eta);
+    if (S_out) OFDFT_CK(cudaMemcpyAsync(S_out, Sg, NH * sizeof(C), cudaMemcpyDeviceToDevice, st));
+    OFDFT_CK(cudaStreamSynchronize(st));
+    ions_set = true;
+    return OFDFT_OK;
+  }
+
+  // One evaluation.  mode 0: density rho; mode 1: psi + t d with scale.
+  // Leaves results in res_d[0..13]; copies them to res_h when sync != 0.
+  int eval(int mode, const T* rho, const T* ps, const T* dd, double t, double scale, double Q, double psid,
+           T* out, cudaStream_t st, bool sync) {
+    Spectra<T> sp = spectra();
+    ProArgs<T> pa{mode, rho, ps, dd, t, scale, cs.alpha};
+    if (sp.nact > 0) {
+      OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+      OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+    }
+    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? vloc : nullptr, Kt, L, Omega, 1.0 / (double)N, g2cut_loc,
+                (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0, partials};
+    if (sp.nact > 0) {
+      OFDFT_RUN("k_xgspace", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_xgspace<T><<<grid_x, kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
+      OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, 1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+    }
+    double* pe = partials + (size_t)grid_x * 4;
+    EpiArgs<T> ea{mode, rho, ps, dd, t, scale, cs.alpha, Te, cs.terms, out, pe};
+    OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+    FinArgs fa{partials, sp.nact > 0 ? grid_x : 0, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mode, res_d};
+    OFDFT_RUN("k_finalize", st, (double)(grid_x * 4 + grid_z * 8) * 8, k_finalize<<<1, 256, 0, st>>>(fa));
+    if (sync) {
+      OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 14 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+    }
+    return OFDFT_OK;
+  }
+
+  int energy_potential(const void* rho, void* v_out, ofdft_energies* e, void* stream_) override {
+    if (!ions_set) { set_error("ofdft_structure_factor must be called before evaluations"); return OFDFT_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream_;
+    int rc = eval(0, (const T*)rho, nullptr, nullptr, 0.0, 1.0, 0.0, 0.0, (T*)v_out, st, e != nullptr);
+    if (rc) return rc;
+    if (e) fill_energies(e);
+    return OFDFT_OK;
+  }
+
+  void fill_energies(ofdft_energies* e) const {
+    e->F_TF = res_h[0]; e->E_vW = res_h[1]; e->E_NL = res_h[2]; e->E_H = res_h[3];
+    e->E_loc = res_h[4]; e->E_xc = res_h[5]; e->E_ion = res_h[6]; e->F_total = res_h[7];
+    e->N_e = res_h[8]; e->mu = res_h[9]; e->residual = res_h[10];
+  }
+
+  // ------------------------------------------------------------------
+  // dot products <V_i, W_j> for host-side use (chunks of kMaxV vectors)
+  int gram(const std::vector<const T*>& V, const std::vector<const T*>& W, std::vector<double>& out,
+           cudaStream_t st) {
+    const int nv = (int)V.size(), nw = (int)W.size();
+    out.assign((size_t)nv * nw, 0.0);
+    std::vector<double> host;
+    for (int c0 = 0; c0 < nv; c0 += kMaxV) {
+      const int cn = std::min(kMaxV, nv - c0);
+      VecList<T> vl{}; vl.nv = cn;
+      for (int i = 0; i < cn; ++i) vl.v[i] = V[c0 + i];
+      VecList<T> wl{}; wl.nv = nw;
+      for (int j = 0; j < nw; ++j) wl.v[j] = W[j];
+      prof.begin("k_gram", st, (double)(cn + nw) * N * sizeof(T));
+      switch (nw) {
+        case 1: k_gram<T, 1><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
+        case 2: k_gram<T, 2><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
+        case 3: k_gram<T, 3><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
+        default: k_gram<T, 4><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
+      }
+      prof.end(st);
+      OFDFT_LAUNCH_CK();
+      int rc;
+      if ((rc = sum_partials(grid_vec, cn * nw, 16, st))) return rc;
+      host.resize((size_t)cn * nw);
+      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, (size_t)cn * nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < cn; ++i)
+        for (int j = 0; j < nw; ++j) out[(size_t)(c0 + i) * nw + j] = res_h[16 + i * nw + j] * dV;
+    }
+    return OFDFT_OK;
+  }
+
+  int minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o, ofdft_result* r, void* stream_) override;
+
+  int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream_) override;
+};
+
+// ---------------------------------------------------------------------------
+// Strong-Wolfe line search (sufficient decrease c1, curvature c2; cubic
+// interpolation in the zoom phase).  phi(t, &f, &slope) evaluates.
+struct LSPoint { double t, f, g; };
+
+static double cubic_min(const LSPoint& a, const LSPoint& b, bool* ok) {
+  const double d1 = a.g + b.g - 3.0 * (a.f - b.f) / (a.t - b.t);
+  const double disc = d1 * d1 - a.g * b.g;
+  if (disc < 0) { *ok = false; return 0; }
+  const double d2 = std::copysign(std::sqrt(disc), b.t - a.t);
+  const double den = b.g - a.g + 2.0 * d2;
+  if (den == 0) { *ok = false; return 0; }
+  *ok = true;
+  return b.t - (b.t - a.t) * (b.g + d2 - d1) / den;
+}
+
+// rel_noise: relative size of rounding noise in the energy; a trial whose
+// energy change is inside it is judged on the slope alone (approximate Wolfe).
+template <typename F>
+static int line_search(F&& phi, double f0, double g0, double t0, double c1, double c2, int max_evals,
+                       double rel_noise, LSPoint* acc, int* evals) {
+  const double eps_f = rel_noise * std::max(1.0, std::fabs(f0));
+  auto armijo = [&](double t, double f) { return f <= f0 + c1 * t * g0 || std::fabs(f - f0) <= eps_f; };
+  auto curv = [&](double g) { return std::fabs(g) <= -c2 * g0; };
+  LSPoint prev{0.0, f0, g0}, lo{}, hi{};
+  double t = t0;
+  *evals = 0;
+  bool bracket = false;
+  while (*evals < max_evals) {
+    LSPoint p{t, 0, 0};
+    int rc = phi(t, &p.f, &p.g);
+    if (rc) return rc;
+    ++*evals;
+    if (!std::isfinite(p.f) || !std::isfinite(p.g)) { lo = prev; hi = p; hi.f = INFINITY; bracket = true; break; }
+    if (!armijo(t, p.f) || (*evals > 1 && p.f >= prev.f && std::fabs(p.f - prev.f) > eps_f)) {
+      lo = prev; hi = p; bracket = true; break;
+    }
+    if (curv(p.g)) { *acc = p; return OFDFT_OK; }
+    if (p.g >= 0) { lo = p; hi = prev; bracket = true; break; }
+    prev = p;
+    t *= 2.0;
+  }
+  if (!bracket) return OFDFT_ERR_NOT_CONVERGED;
+  while (*evals < max_evals) {
+    bool ok = false;
+    double tc = 0;
+    if (std::isfinite(hi.f)) tc = cubic_min(lo, hi, &ok);
+    const double left = std::min(lo.t, hi.t), right = std::max(lo.t, hi.t), w = right - left;
+    if (!ok || !(tc >= left + 0.1 * w && tc <= right - 0.1 * w)) tc = 0.5 * (lo.t + hi.t);
+    LSPoint p{tc, 0, 0};
+    int rc = phi(tc, &p.f, &p.g);
+    if (rc) return rc;
+    ++*evals;
+    if (!std::isfinite(p.f) || !armijo(tc, p.f) || (p.f >= lo.f && std::fabs(p.f - lo.f) > eps_f)) {
+      hi = p;
+      if (!std::isfinite(p.f)) hi.f = INFINITY;
+    } else {
+      if (curv(p.g)) { *acc = p; return OFDFT_OK; }
+      if (p.g * (hi.t - lo.t) >= 0) hi = lo;
+      lo = p;
+    }
+    if (std::fabs(hi.t - lo.t) < 1e-16 * std::max(1.0, std::fabs(lo.t))) break;
+  }
+  return OFDFT_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// L-BFGS on psi with n = N_e psi^2 / Q.  The two-loop recursion is carried
+// out on scalars from the Gram matrices of the history; the direction is
+// then one linear-combination pass.
+template <typename T>
+int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o, ofdft_result* r, void* stream_) {
+  if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_minimize"); return OFDFT_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream_;
+  const int m = std::min(o.m, m_max);
+  if (m < 1) { set_error("L-BFGS memory must be >= 1"); return OFDFT_ERR_INVALID; }
+  const double n_ion = (double)cs.Z.size();
+  const char* trace_env = std::getenv("OFDFT_TRACE");
+  const bool trace = trace_env && trace_env[0] == '1';
+  int rc;
+  if (start_uniform) OFDFT_RUN("k_fill", st, (double)N * sizeof(T), k_fill<T><<<grid_vec, kThreads, 0, st>>>(psi, (T)std::sqrt(nbar), N));
+  else OFDFT_RUN("k_sqrt_clamp", st, 2.0 * N * sizeof(T), k_sqrt_clamp<T><<<grid_vec, kThreads, 0, st>>>(psi, (const T*)rho_io, N));
+  std::vector<double> dots;
+  if ((rc = gram({psi}, {psi}, dots, st))) return rc;
+  double Qcur = dots[0];
+  if (!(Qcur > 0)) { set_error("initial density has zero norm"); return OFDFT_ERR_INVALID; }
+  int evals = 0;
+  // evaluation at the starting point (t = 0; d is unused, psi stands in)
+  if ((rc = eval(1, nullptr, psi, psi, 0.0, Ne / Qcur, Qcur, Qcur, gp, st, true))) return rc;
+  ++evals;
+  double F = res_h[7];
+  double energies[14];
+  std::memcpy(energies, res_h, sizeof(energies));
+  if (!std::isfinite(F) || res_h[13] > 0) { set_error("non-finite energy at the starting density"); return OFDFT_ERR_NAN; }
+  OFDFT_RUN("k_project", st, 3.0 * N * sizeof(T), k_project<T><<<grid_vec, kThreads, 0, st>>>(g, gp, psi, Ne / Qcur, res_h[9], N));
+
+  Ring ring; ring.m = m;
+  std::vector<double> SY((size_t)kMaxMem * kMaxMem, 0.0), YY((size_t)kMaxMem * kMaxMem, 0.0);
+  auto sy = [&](int a, int b) -> double& { return SY[(size_t)a * kMaxMem + b]; };
+  auto yy = [&](int a, int b) -> double& { return YY[(size_t)a * kMaxMem + b]; };
+  int new_slot = -1;
+  int small = 0, it = 0;
+  bool converged = false;
+  for (it = 1; it <= o.max_iter; ++it) {
+    // --- one pass: V = [g, psi, S_0..S_k-1, Y_0..Y_k-1], W = [g, psi, s_new, y_new]
+    const int k = ring.count;
+    std::vector<const T*> V{g, psi};
+    for (int i = 0; i < k; ++i) V.push_back(Sh[ring.slot(i)]);
+    for (int i = 0; i < k; ++i) V.push_back(Yh[ring.slot(i)]);
+    std::vector<const T*> W{g, psi};
+    if (new_slot >= 0) { W.push_back(Sh[new_slot]); W.push_back(Yh[new_slot]); }
+    if ((rc = gram(V, W, dots, st))) return rc;
+    const int nw = (int)W.size();
+    auto dt = [&](int vi, int wj) { return dots[(size_t)vi * nw + wj]; };
+    const double gg = dt(0, 0);
+    Qcur = dt(1, 1);
+    std::vector<double> Sg(k), Yg(k);
+    for (int i = 0; i < k; ++i) { Sg[i] = dt(2 + i, 0); Yg[i] = dt(2 + k + i, 0); }
+    if (new_slot >= 0) {
+      for (int i = 0; i < k; ++i) {
+        const int si = ring.slot(i);
+        sy(si, new_slot) = dt(2 + i, 3);          // <s_i, y_new>
+        sy(new_slot, si) = dt(2 + k + i, 2);      // <s_new, y_i>
+        yy(si, new_slot) = dt(2 + k + i, 3);      // <y_i, y_new>
+        yy(new_slot, si) = yy(si, new_slot);
+      }
+      if (!(sy(new_slot, new_slot) > 0)) ring.clear();   // curvature lost to rounding: restart
+      new_slot = -1;
+    }
+    const int kk = ring.count;
+    // --- two-loop recursion carried out on the Gram scalars
+    std::vector<double> alpha(kk, 0.0), beta(kk, 0.0), rho(kk, 0.0);
+    for (int i = 0; i < kk; ++i) rho[i] = 1.0 / sy(ring.slot(i), ring.slot(i));
+    for (int i = kk - 1; i >= 0; --i) {
+      double sq = Sg[i];
+      for (int j = i + 1; j < kk; ++j) sq -= alpha[j] * sy(ring.slot(i), ring.slot(j));
+      alpha[i] = rho[i] * sq;
+    }
+    double gamma = 1.0, t0 = 1.0;
+    if (kk > 0) {
+      const int sl = ring.slot(kk - 1);
+      gamma = sy(sl, sl) / yy(sl, sl);
+    } else {
+      t0 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
+    }
+    for (int i = 0; i < kk; ++i) {
+      double yr = Yg[i];
+      for (int j = 0; j < kk; ++j) yr -= alpha[j] * yy(ring.slot(i), ring.slot(j));
+      yr *= gamma;
+      for (int j = 0; j < i; ++j) yr += (alpha[j] - beta[j]) * sy(ring.slot(j), ring.slot(i));
+      beta[i] = rho[i] * yr;
+    }
+    // d = -gamma g + gamma sum alpha_j y_j - sum (alpha_j - beta_j) s_j
+    VecList<T> vl{};
+    vl.nv = 0;
+    vl.v[vl.nv] = g; vl.c[vl.nv++] = -gamma;
+    for (int j = 0; j < kk; ++j) {
+      vl.v[vl.nv] = Yh[ring.slot(j)]; vl.c[vl.nv++] = gamma * alpha[j];
+      vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]);
+    }
+    double dd = 0, dg = 0, dpsi = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      OFDFT_RUN("k_lincomb", st, (double)(vl.nv + 3) * N * sizeof(T), k_lincomb<T><<<grid_vec, kThreads, 0, st>>>(vl, d, g, psi, N, partials));
+      if ((rc = sum_partials(grid_vec, 3, 16, st))) return rc;
+      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+      dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
+      if (dg < 0 || attempt == 1) break;
+      // not a descent direction: drop the history and restart along -g
+      ring.clear();
+      vl.nv = 1; vl.v[0] = g; vl.c[0] = -1.0;
+      t0 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
+    }
+    if (!(dg < 0)) break;
+    // --- strong-Wolfe line search along d
+    double lastScale = 0, lastMu = 0, lastE[14];
+    auto phi = [&](double t, double* f, double* slope) -> int {
+      const double Qt = Qcur + 2.0 * t * dpsi + t * t * dd;
+      const double sc = Ne / Qt;
+      int e = eval(1, nullptr, psi, d, t, sc, Qt, dpsi + t * dd, gp, st, true);
+      if (e) return e;
+      ++evals;
+      *f = res_h[13] > 0 ? NAN : res_h[7];
+      *slope = res_h[11];
+      lastScale = sc; lastMu = res_h[9];
+      std::memcpy(lastE, res_h, sizeof(lastE));
+      return OFDFT_OK;
+    };
+    LSPoint acc{};
+    int lsev = 0;
+    // energy noise: FP64 rounding, or FP32 terms summed in FP64
+    const double rel_noise = sizeof(T) == 4 ? 1e-7 : 1e-14;
+    rc = line_search(phi, F, dg, t0, o.c1, o.c2, 40, rel_noise, &acc, &lsev);
+    if (trace)
+      std::fprintf(stderr, "ofdft it %4d F %.12f dphi0 %.3e t %.3e ls_evals %d status %d R %.3e hist %d\n", it,
+                   rc == OFDFT_OK ? acc.f : F, dg, acc.t, lsev, rc, lastE[10], ring.count);
+    if (rc == OFDFT_ERR_NOT_CONVERGED) break;
+    if (rc) return rc;
+    // --- accept: s = t d, y = g_t - g, psi += t d, g = g_t  (the last trial is the accepted one)
+    const int slot = ring.push();
+    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, acc.t, gp, lastScale, lastMu, g, Sh[slot], Yh[slot], N));
+    new_slot = slot;
+    const double dF = std::fabs(acc.f - F) / n_ion;
+    F = acc.f;
+    std::memcpy(energies, lastE, sizeof(energies));
+    small = dF < o.tol_F_per_ion ? small + 1 : 0;
+    if (small >= 3 && lastE[10] < o.tol_residual) { converged = true; break; }
+  }
+  // output density n = N_e psi^2 / int psi^2
+  std::vector<double> qd;
+  if ((rc = gram({psi}, {psi}, qd, st))) return rc;
+  OFDFT_RUN("k_density", st, 2.0 * N * sizeof(T), k_density<T><<<grid_vec, kThreads, 0, st>>>((T*)rho_io, psi, Ne / qd[0], N));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  const int status = converged ? OFDFT_OK : OFDFT_ERR_NOT_CONVERGED;
+  if (r) {
+    std::memcpy(res_h, energies, sizeof(energies));
+    fill_energies(&r->e);
+    r->iterations = std::min(it, o.max_iter);
+    r->evaluations = evals;
+    r->status = status;
+  }
+  if (!converged) set_error("minimiser stopped before reaching the tolerances");
+  return status;
+}
+
+
+// ---------------------------------------------------------------------------
+// Electron-ion static structure factor on the first n_shells distinct nonzero
+// |m|^2 shells (one snapshot).
+template <typename T>
+int Engine<T>::sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream_) {
+  if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_sei_shells"); return OFDFT_ERR_INVALID; }
+  if (n_shells < 1 || n_shells > 4096) { set_error("n_shells must be in [1, 4096]"); return OFDFT_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream_;
+  // distinct nonzero m^2 present on the grid, ascending, and their entries
+  const int lim = n / 2;
+  std::vector<char> present(3 * lim * lim + 1, 0);
+  for (int mx = -lim; mx < lim; ++mx)
+    for (int my = -lim; my < lim; ++my)
+      for (int mz = 0; mz <= lim; ++mz) {
+        const int m2 = mx * mx + my * my + mz * mz;
+        if (m2 > 0) present[m2] = 1;
+      }
+  std::vector<int> shell_m2;
+  for (int m2 = 1; m2 < (int)present.size() && (int)shell_m2.size() < n_shells; ++m2)
+    if (present[m2]) shell_m2.push_back(m2);
+  const int ns = (int)shell_m2.size();
+  if (ns < n_shells) { set_error("grid has fewer distinct shells than requested"); return OFDFT_ERR_INVALID; }
+  const int m2max = shell_m2.back();
+  if ((2.0 * kPi / L) * (2.0 * kPi / L) * m2max > std::max(156.0 / (cs.rc * cs.rc), (2.0 * kPi / L) * (2.0 * kPi / L) * 600.0)) {
+    set_error("requested shells extend beyond the stored structure factor");
+    return OFDFT_ERR_INVALID;
+  }
+  std::vector<int> shell_of(m2max + 1, -1);
+  for (int i = 0; i < ns; ++i) shell_of[shell_m2[i]] = i;
+  std::vector<std::vector<long long>> lists(ns);
+  std::vector<std::vector<float>> wl(ns);
+  const int r = (int)std::ceil(std::sqrt((double)m2max));
+  for (int mx = -std::min(r, lim); mx <= std::min(r, lim - 1); ++mx)
+    for (int my = -std::min(r, lim); my <= std::min(r, lim - 1); ++my)
+      for (int mz = 0; mz <= std::min(r, lim); ++mz) {
+        const int m2 = mx * mx + my * my + mz * mz;
+        if (m2 == 0 || m2 > m2max || shell_of[m2] < 0) continue;
+        const int kx = mx < 0 ? mx + n : mx, ky = my < 0 ? my + n : my;
+        const long long q = ((long long)kx * n + ky) * nh + mz;
+        lists[shell_of[m2]].push_back(q);
+        wl[shell_of[m2]].push_back((mz == 0 || 2 * mz == n) ? 1.0f : 2.0f);
+      }
+  std::vector<int> ptr(ns + 1, 0);
+  std::vector<long long> idx;
+  std::vector<float> wts;
+  for (int i = 0; i < ns; ++i) {
+    ptr[i + 1] = ptr[i] + (int)lists[i].size();
+    idx.insert(idx.end(), lists[i].begin(), lists[i].end());
+    wts.insert(wts.end(), wl[i].begin(), wl[i].end());
+  }
+  int* ptr_d = nullptr; long long* idx_d = nullptr; float* w_d = nullptr; double* out_d = nullptr;
+  OFDFT_CK(cudaMallocAsync((void**)&ptr_d, ptr.size() * sizeof(int), st));
+  OFDFT_CK(cudaMallocAsync((void**)&idx_d, std::max<size_t>(1, idx.size()) * sizeof(long long), st));
+  OFDFT_CK(cudaMallocAsync((void**)&w_d, std::max<size_t>(1, wts.size()) * sizeof(float), st));
+  OFDFT_CK(cudaMallocAsync((void**)&out_d, 2 * (size_t)ns * sizeof(double), st));
+  OFDFT_CK(cudaMemcpyAsync(ptr_d, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaMemcpyAsync(idx_d, idx.data(), idx.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaMemcpyAsync(w_d, wts.data(), wts.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  // forward transform of rho into spec[0]
+  Spectra<T> sp{};
+  sp.s[0] = spec[0]; sp.nact = 1; sp.idx[0] = 0;
+  ProArgs<T> pa{0, (const T*)rho, nullptr, nullptr, 0.0, 1.0, cs.alpha};
+  const int mode = 0;
+  OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+  OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+  OFDFT_RUN("k_xpass", st, 2.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 1), kThreads, smem_x, st>>>(sp, pn, tw_n, n, xJ));
+  const double nion = (double)cs.Z.size();
+  const double scale = Omega / (double)N / std::sqrt(Ne * nion);
+  OFDFT_RUN("k_sei_shells", st, (double)idx.size() * (2 * sizeof(C) + 12), k_sei_shells<T><<<ns, 256, 0, st>>>(spec[0], Sg, ptr_d, idx_d, w_d, scale, out_d));
+  std::vector<double> hout(2 * (size_t)ns);
+  OFDFT_CK(cudaMemcpyAsync(hout.data(), out_d, hout.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  OFDFT_CK(cudaFreeAsync(ptr_d, st));
+  OFDFT_CK(cudaFreeAsync(idx_d, st));
+  OFDFT_CK(cudaFreeAsync(w_d, st));
+  OFDFT_CK(cudaFreeAsync(out_d, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < ns; ++i) {
+    q_out[i] = 2.0 * kPi / L * std::sqrt((double)shell_m2[i]);
+    s_out[i] = hout[2 * i] / hout[2 * i + 1];
+  }
+  return OFDFT_OK;
+}
+
+}  // namespace ofdft

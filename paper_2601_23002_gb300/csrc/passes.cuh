@@ -1,0 +1,501 @@
+// The per-evaluation kernels of the functional (templated on the real type T).
+//
+// One evaluation of F[n] and its potential is five launches over the grid:
+//   1. k_zfwd      prologue (n, n^a, psi from rho or from psi + t d) fused with
+//                  the real-to-complex FFT along z (half-length complex FFT).
+//   2. k_ypass<-1> complex FFT along y.
+//   3. k_xgspace   FFT along x, every G-space term (Hartree + local
+//                  pseudopotential, nonlocal kernel K(|G|), vW |G|^2) with its
+//                  FP64 energy partial sums, inverse FFT along x.
+//   4. k_ypass<+1> inverse FFT along y.
+//   5. k_zinv_epi  complex-to-real FFT along z fused with the pointwise
+//                  functional (finite-T TF through the inverse Fermi-Dirac
+//                  integral, PZ LDA XC, v_NL) and the potential / gradient.
+// plus k_finalize, a one-block FP64 reduction of the per-block partial sums.
+//
+// Layouts: real fields [n][n][n] (z fastest); half spectra [n][n][n/2+1].
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+#include "fd_fit_tables.h"
+
+namespace ofdft {
+
+constexpr double kNmin = 1e-20;        // density floor in powers and logarithms
+constexpr double kPhiMin = 1e-10;      // sqrt(n) floor in the vW potential
+
+enum : int { FIELD_N = 1, FIELD_NA = 2, FIELD_PSI = 4 };
+
+template <typename T> struct Spectra {
+  cplx<T>* s[3];    // by field index 0 = n, 1 = n^a, 2 = psi
+  int nact;         // number of active fields
+  int idx[3];       // active field indices, in order
+};
+
+// ---------------------------------------------------------------------------
+// Finite-temperature Thomas-Fermi pointwise: eta(y) and p(y) from the
+// piecewise Chebyshev tables (see gen_fd_fits.py); f_TF = n T (eta - p),
+// v_TF = T eta.
+static __device__ __forceinline__ void fd_eta_p(double y, double& eta, double& p) {
+  const double s = log(y);
+  const double lngamma32 = -0.12078223763524522234551844578164;  // ln Gamma(3/2)
+  if (s < FD_S_LO) {
+    const double u = y * 1.1283791670955125738961589031215;      // y / Gamma(3/2)
+    eta = s - lngamma32 + u * 0.35355339059327376220042218105242;   // + u / 2^(3/2)
+    p = 1.0 + u * 0.17677669529663688110021109052621;               // 1 + u / 2^(5/2)
+  } else if (s >= FD_S_HI) {
+    const double e0 = pow(1.5 * y, 2.0 / 3.0);
+    eta = e0 * (1.0 - 0.82246703342411321823620758332301 / (e0 * e0));   // pi^2/12
+    p = 0.4 * eta * (1.0 + 4.9348022005446793094172454999381 / (eta * eta));  // pi^2/2
+  } else {
+    const double r = (s - FD_S_LO) / FD64_W;
+    int i = (int)r;
+    i = i < 0 ? 0 : (i >= FD64_NINT ? FD64_NINT - 1 : i);
+    const double x = 2.0 * (r - (double)i) - 1.0;
+    const double* ce = fd64_eta[i];
+    const double* cp = fd64_p[i];
+    double b1 = 0, b2 = 0, c1 = 0, c2 = 0;
+#pragma unroll
+    for (int k = FD64_NC - 1; k >= 1; --k) {
+      const double t = fma(2.0 * x, b1, ce[k] - b2); b2 = b1; b1 = t;
+      const double u = fma(2.0 * x, c1, cp[k] - c2); c2 = c1; c1 = u;
+    }
+    eta = fma(x, b1, ce[0] - b2);
+    p = fma(x, c1, cp[0] - c2);
+  }
+}
+
+static __device__ __forceinline__ void fd_eta_p(float y, float& eta, float& p) {
+  const float s = logf(y);
+  const float lngamma32 = -0.120782237635245222f;
+  if (s < (float)FD_S_LO) {
+    const float u = y * 1.12837916709551257f;
+    eta = s - lngamma32 + u * 0.353553390593273762f;
+    p = 1.0f + u * 0.176776695296636881f;
+  } else if (s >= (float)FD_S_HI) {
+    const float e0 = powf(1.5f * y, 2.0f / 3.0f);
+    eta = e0 * (1.0f - 0.822467033424113218f / (e0 * e0));
+    p = 0.4f * eta * (1.0f + 4.93480220054467931f / (eta * eta));
+  } else {
+    const float r = (s - (float)FD_S_LO) * (1.0f / FD32_W);
+    int i = (int)r;
+    i = i < 0 ? 0 : (i >= FD32_NINT ? FD32_NINT - 1 : i);
+    const float x = 2.0f * (r - (float)i) - 1.0f;
+    const float* ce = fd32_eta[i];
+    const float* cp = fd32_p[i];
+    float b1 = 0, b2 = 0, c1 = 0, c2 = 0;
+#pragma unroll
+    for (int k = FD32_NC - 1; k >= 1; --k) {
+      const float t = fmaf(2.0f * x, b1, ce[k] - b2); b2 = b1; b1 = t;
+      const float u = fmaf(2.0f * x, c1, cp[k] - c2); c2 = c1; c1 = u;
+    }
+    eta = fmaf(x, b1, ce[0] - b2);
+    p = fmaf(x, c1, cp[0] - c2);
+  }
+}
+
+// Perdew-Zunger LDA, unpolarised: returns e_xc per electron, v_xc.
+template <typename T>
+__device__ __forceinline__ void pz81(T n, T& exc, T& vxc) {
+  const T third = (T)(1.0 / 3.0);
+  const T cbn = cbrt(n);
+  // r_s = (3 / (4 pi n))^(1/3)
+  const T rs = (T)0.62035049089940001666800681204778 / cbn;
+  const T ex = (T)-0.73855876638202240588423003268 * cbn;   // -(3/4)(3/pi)^(1/3) n^(1/3)
+  const T vx = (T)(4.0 / 3.0) * ex;
+  T ec, vc;
+  if (rs >= (T)1) {
+    const T g = (T)-0.1423, b1 = (T)1.0529, b2 = (T)0.3334;
+    const T sq = sqrt(rs);
+    const T den = (T)1 + b1 * sq + b2 * rs;
+    ec = g / den;
+    vc = ec * ((T)1 + (T)(7.0 / 6.0) * b1 * sq + (T)(4.0 / 3.0) * b2 * rs) / den;
+  } else {
+    const T A = (T)0.0311, B = (T)-0.048, C = (T)0.0020, D = (T)-0.0116;
+    const T ln = log(rs);
+    ec = A * ln + B + C * rs * ln + D * rs;
+    vc = A * ln + (B - A * third) + (T)(2.0 / 3.0) * C * rs * ln + ((T)2 * D - C) * third * rs;
+  }
+  exc = ex + ec;
+  vxc = vx + vc;
+}
+
+template <typename T> __device__ __forceinline__ T pow_t(T a, T b);
+template <> __device__ __forceinline__ double pow_t<double>(double a, double b) { return pow(a, b); }
+template <> __device__ __forceinline__ float pow_t<float>(float a, float b) { return exp2f(b * log2f(a)); }
+
+// ---------------------------------------------------------------------------
+// 1. prologue + R2C along z
+template <typename T> struct ProArgs {
+  int mode;            // 0: density rho given; 1: psi + t d with n = scale psi^2
+  const T* rho;
+  const T* psi;
+  const T* d;
+  double t, scale, alpha;
+};
+
+// smem: psit[R][n] (T) | buf0[R][P] | buf1[R][P] (complex)
+template <typename T>
+__global__ void __launch_bounds__(256) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPlan1 ph,
+                                              const cplx<T>* __restrict__ tw_h,
+                                              const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int h = n / 2, nh = h + 1;
+  T* psit = reinterpret_cast<T*>(smem_raw);
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)R * n * sizeof(T) + 15) & ~(size_t)15));
+  cplx<T>* buf1 = buf0 + (size_t)R * P;
+  const size_t row0 = (size_t)blockIdx.x * R;
+  R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
+  const size_t off = row0 * n;
+  const int tot = R * n;
+  // psi_t (or sqrt rho) for the block's rows
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    T v;
+    if (a.mode == 0) v = sqrt(fmax(a.rho[off + q], (T)0));
+    else v = a.psi[off + q] + (T)a.t * a.d[off + q];
+    psit[q] = v;
+  }
+  __syncthreads();
+  const T scale = (T)a.scale, alpha = (T)a.alpha, nmin = (T)kNmin;
+  for (int f = 0; f < sp.nact; ++f) {
+    const int fid = sp.idx[f];
+    for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
+      const int r = q / h, k = q % h;
+      T x0 = psit[r * n + 2 * k], x1 = psit[r * n + 2 * k + 1];
+      if (fid == 0) {
+        if (a.mode == 0) { x0 = a.rho[off + r * n + 2 * k]; x1 = a.rho[off + r * n + 2 * k + 1]; }
+        else { x0 = scale * x0 * x0; x1 = scale * x1 * x1; }
+      } else if (fid == 1) {
+        T n0, n1;
+        if (a.mode == 0) { n0 = a.rho[off + r * n + 2 * k]; n1 = a.rho[off + r * n + 2 * k + 1]; }
+        else { n0 = scale * x0 * x0; n1 = scale * x1 * x1; }
+        x0 = pow_t<T>(fmax(n0, nmin), alpha);
+        x1 = pow_t<T>(fmax(n1, nmin), alpha);
+      }
+      buf0[r * P + k] = mk<T>(x0, x1);
+    }
+    __syncthreads();
+    cplx<T>* Z = fft_smem<T, -1>(buf0, buf1, ph, 1, P, R, tw_h);
+    // X[k] = (Z[k] + Z*[h-k])/2 - (i/2) W^k (Z[k] - Z*[h-k]),  k = 0..h
+    cplx<T>* out = sp.s[fid] + row0 * nh;
+    for (int q = threadIdx.x; q < R * nh; q += blockDim.x) {
+      const int r = q / nh, k = q % nh;
+      const cplx<T> zk = Z[r * P + (k == h ? 0 : k)];
+      const cplx<T> zc = cconj(Z[r * P + (k == 0 ? 0 : h - k)]);
+      const cplx<T> e = cadd(zk, zc);
+      const cplx<T> o = csub(zk, zc);
+      const cplx<T> w = tw_n[k];
+      const cplx<T> wo = cmul(w, o);
+      // -(i/2) wo = (wo.y/2, -wo.x/2)
+      out[q] = mk<T>((T)0.5 * (e.x + wo.y), (T)0.5 * (e.y - wo.x));
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2./4. FFT along y, in place.  Tile: all n values of y times J consecutive kz
+// at one x.  grid.x = n * ceil(nh / J), grid.y = active field.
+// smem: buf0[n][J] | buf1[n][J]
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) k_ypass(Spectra<T> sp, FftPlan1 pn, const cplx<T>* __restrict__ tw_n,
+                                               int n, int J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* buf1 = buf0 + (size_t)n * J;
+  const int nh = n / 2 + 1;
+  const int ntz = (nh + J - 1) / J;
+  const int x = blockIdx.x / ntz, tz = blockIdx.x % ntz;
+  const int kz0 = tz * J;
+  const int jn = min(J, nh - kz0);
+  cplx<T>* base = sp.s[sp.idx[blockIdx.y]] + (size_t)x * n * nh + kz0;
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int y = q / J, j = q % J;
+    buf0[q] = j < jn ? base[(size_t)y * nh + j] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  cplx<T>* res = fft_smem<T, DIR>(buf0, buf1, pn, J, 1, J, tw_n);
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int y = q / J, j = q % J;
+    if (j < jn) base[(size_t)y * nh + j] = res[q];
+  }
+}
+
+// FFT along x only (no G-space work), in place; used for analysis transforms.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) k_xpass(Spectra<T> sp, FftPlan1 pn, const cplx<T>* __restrict__ tw_n,
+                                               int n, int J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* buf1 = buf0 + (size_t)n * J;
+  const int nh = n / 2 + 1;
+  const size_t plane = (size_t)n * nh;
+  const size_t j0 = (size_t)blockIdx.x * J;
+  const int jn = (int)min((size_t)J, plane - j0);
+  cplx<T>* base = sp.s[sp.idx[blockIdx.y]] + j0;
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int kx = q / J, j = q % J;
+    buf0[q] = j < jn ? base[(size_t)kx * plane + j] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  cplx<T>* res = fft_smem<T, DIR>(buf0, buf1, pn, J, 1, J, tw_n);
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int kx = q / J, j = q % J;
+    if (j < jn) base[(size_t)kx * plane + j] = res[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. FFT along x + G-space terms + inverse FFT along x.
+// Tile: all n values of kx times J consecutive flattened (ky, kz).
+template <typename T> struct GArgs {
+  const cplx<T>* vloc;   // V_loc(G), half spectrum (may be null: no local term)
+  const T* K;            // K(m^2) table
+  double L, Omega;
+  double invN;
+  double g2cut_loc;      // V_loc negligible beyond this |G|^2
+  int hartree;           // 1: add 4 pi n~/G^2 to the n field
+  double* partials;      // [gridDim.x][4]: E_H, E_loc, E_NL, E_vW(raw)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftPlan1 pn,
+                                                 const cplx<T>* __restrict__ tw_n, int n, int J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[4 * 32];
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* buf1 = buf0 + (size_t)n * J;
+  const int nh = n / 2 + 1;
+  const size_t plane = (size_t)n * nh;   // stride between consecutive kx
+  const size_t j0 = (size_t)blockIdx.x * J;
+  const int jn = (int)min((size_t)J, plane - j0);
+  const double twopiL = 2.0 * kPi / g.L;
+  double acc[4] = {0, 0, 0, 0};
+  for (int f = 0; f < sp.nact; ++f) {
+    const int fid = sp.idx[f];
+    cplx<T>* base = sp.s[fid] + j0;
+    for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+      const int kx = q / J, j = q % J;
+      buf0[q] = j < jn ? base[(size_t)kx * plane + j] : mk<T>(0, 0);
+    }
+    __syncthreads();
+    cplx<T>* F = fft_smem<T, -1>(buf0, buf1, pn, J, 1, J, tw_n);
+    for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+      const int kx = q / J, j = q % J;
+      if (j >= jn) { F[q] = mk<T>(0, 0); continue; }
+      const size_t jj = j0 + j;
+      const int ky = (int)(jj / nh), kz = (int)(jj % nh);
+      const int mx = kx <= n / 2 - 1 ? kx : kx - n;
+      const int my = ky <= n / 2 - 1 ? ky : ky - n;
+      const int m2 = mx * mx + my * my + kz * kz;
+      const double G2 = twopiL * twopiL * (double)m2;
+      const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+      const cplx<T> v = F[q];
+      const double vr = (double)v.x * g.invN, vi = (double)v.y * g.invN;   // f~(G)
+      const double a2 = vr * vr + vi * vi;
+      cplx<T> o;
+      if (fid == 0) {
+        double orr = 0, oi = 0;
+        if (g.hartree && m2 > 0) {
+          const double c = 4.0 * kPi / G2;
+          acc[0] += w * 0.5 * g.Omega * c * a2;
+          orr = c * vr; oi = c * vi;
+        }
+        if (g.vloc && G2 <= g.g2cut_loc) {
+          const cplx<T> vl = g.vloc[(size_t)kx * plane + jj];
+          acc[1] += w * g.Omega * (vr * (double)vl.x + vi * (double)vl.y);
+          orr += (double)vl.x; oi += (double)vl.y;
+        }
+        o = mk<T>((T)orr, (T)oi);
+      } else if (fid == 1) {
+        const double k = (double)g.K[m2];
+        acc[2] += w * g.Omega * k * a2;
+        o = mk<T>((T)(k * vr), (T)(k * vi));
+      } else {
+        acc[3] += w * 0.5 * g.Omega * G2 * a2;
+        o = mk<T>((T)(G2 * vr), (T)(G2 * vi));
+      }
+      F[q] = o;
+    }
+    __syncthreads();
+    cplx<T>* other = (F == buf0) ? buf1 : buf0;
+    cplx<T>* res = fft_smem<T, +1>(F, other, pn, J, 1, J, tw_n);
+    for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+      const int kx = q / J, j = q % J;
+      if (j < jn) base[(size_t)kx * plane + j] = res[q];
+    }
+    __syncthreads();
+  }
+  double out[4];
+  block_sum<4>(acc, red, out);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g.partials[(size_t)blockIdx.x * 4 + q] = out[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. C2R along z + pointwise functional.
+template <typename T> struct EpiArgs {
+  int mode;              // 0: density given (write v); 1: psi + t d (write g')
+  const T* rho;
+  const T* psi;
+  const T* d;
+  double t, scale, alpha, T_e;
+  int terms;             // OFDFT_TERM_* mask
+  T* out;                // v (mode 0) or g' = psi_t v_rest + lap/2 (mode 1); may be null
+  double* partials;      // [gridDim.x][8]
+};
+
+// smem: realf[3][R][n] (T) | buf0[R][P] | buf1[R][P]
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, FftPlan1 ph,
+                                                  const cplx<T>* __restrict__ tw_h,
+                                                  const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[8 * 32];
+  const int h = n / 2, nh = h + 1;
+  T* realf = reinterpret_cast<T*>(smem_raw);
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)3 * R * n * sizeof(T) + 15) & ~(size_t)15));
+  cplx<T>* buf1 = buf0 + (size_t)R * P;
+  // (realf is laid out for the full R rows; a short last block uses a prefix)
+  const size_t row0 = (size_t)blockIdx.x * R;
+  const int Rfull = R;
+  R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
+  const int tot = R * n;
+  for (int f = 0; f < sp.nact; ++f) {
+    const int fid = sp.idx[f];
+    const cplx<T>* in = sp.s[fid] + row0 * nh;
+    // Z[k] = (X[k] + X*[h-k]) + i W^-k (X[k] - X*[h-k]),  k = 0..h-1
+    for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
+      const int r = q / h, k = q % h;
+      const cplx<T> xk = in[(size_t)r * nh + k];
+      const cplx<T> xc = cconj(in[(size_t)r * nh + (h - k)]);
+      const cplx<T> e = cadd(xk, xc);
+      const cplx<T> o = cmul(cconj(tw_n[k]), csub(xk, xc));
+      buf0[r * P + k] = mk<T>(e.x - o.y, e.y + o.x);   // e + i o
+    }
+    __syncthreads();
+    cplx<T>* z = fft_smem<T, +1>(buf0, buf1, ph, 1, P, R, tw_h);
+    T* dst = realf + (size_t)fid * Rfull * n;
+    for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
+      const int r = q / h, k = q % h;
+      const cplx<T> v = z[r * P + k];
+      dst[r * n + 2 * k] = v.x;
+      dst[r * n + 2 * k + 1] = v.y;
+    }
+    __syncthreads();
+  }
+  // pointwise functional
+  const bool has_n = sp.s[0] != nullptr, has_na = sp.s[1] != nullptr, has_psi = sp.s[2] != nullptr;
+  const T* fH = realf;
+  const T* fK = realf + (size_t)Rfull * n;
+  const T* fL = realf + 2 * (size_t)Rfull * n;
+  const size_t off = row0 * n;
+  const T Te = (T)a.T_e;
+  const T cy = (T)(9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * pow(a.T_e, 1.5)));
+  const T alpha = (T)a.alpha, nmin = (T)kNmin;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    T psit, nval;
+    if (a.mode == 0) {
+      nval = a.rho[off + q];
+      psit = sqrt(fmax(nval, (T)0));
+    } else {
+      psit = a.psi[off + q] + (T)a.t * a.d[off + q];
+      nval = (T)a.scale * psit * psit;
+    }
+    const T nf = fmax(nval, nmin);
+    T vrest = 0;
+    if (a.terms & 1) {              // TF
+      T eta, p;
+      fd_eta_p(nf * cy, eta, p);
+      vrest += Te * eta;
+      acc[0] += (double)(nf * Te * (eta - p));
+    }
+    if (a.terms & 8) {              // XC
+      T exc, vxc;
+      pz81<T>(nf, exc, vxc);
+      vrest += vxc;
+      acc[1] += (double)(nval * exc);
+    }
+    if (has_n) vrest += fH[q];
+    if (has_na) vrest += (T)2 * alpha * pow_t<T>(nf, alpha - (T)1) * fK[q];
+    const T lap = has_psi ? fL[q] : (T)0;   // -lap(psi)
+    acc[2] += (double)vrest * (double)nval;
+    acc[6] += (double)nval;
+    if (a.mode == 0) {
+      const T phi = fmax(psit, (T)kPhiMin);
+      const T v = vrest + lap / ((T)2 * phi);
+      if (a.out) a.out[off + q] = v;
+      // residual pieces with psi = sqrt(rho), scale 1: g' = psi v_rest + lap/2
+      const T gp = psit * vrest + (T)0.5 * lap;
+      acc[4] += (double)gp * (double)gp;
+      acc[5] += (double)gp * (double)psit;
+      if (!isfinite((double)v)) acc[7] += 1.0;
+    } else {
+      const T gp = psit * vrest + (T)0.5 * lap;
+      if (a.out) a.out[off + q] = gp;
+      acc[3] += (double)gp * (double)a.d[off + q];
+      acc[4] += (double)gp * (double)gp;
+      acc[5] += (double)gp * (double)psit;
+      if (!isfinite((double)gp)) acc[7] += 1.0;
+    }
+  }
+  double out8[8];
+  block_sum<8>(acc, red, out8);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a.partials[(size_t)blockIdx.x * 8 + q] = out8[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-block reduction of partial sums (fixed order: deterministic).
+// res[]: 0 F_TF 1 E_vW 2 E_NL 3 E_H 4 E_loc 5 E_xc 6 E_ion 7 F_total 8 N_e 9 mu
+//        10 residual 11 slope <g, d> 12 int v_rest n 13 nonfinite count
+struct FinArgs {
+  const double* pg; int ng;     // G-space partials [ng][4]
+  const double* pe; int ne;     // epilogue partials [ne][8]
+  double dV, E_ion, Ne, scale, Q;  // Q = int psi_t^2 (mode 1); scale = N_e / Q
+  double psid;                  // <psi_t, d> (mode 1)
+  int mode;
+  double* res;
+};
+
+static __global__ void __launch_bounds__(256) k_finalize(FinArgs f) {
+  __shared__ double red[12 * 32];
+  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < f.ng; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += f.pg[(size_t)b * 4 + q];
+  }
+  for (int b = threadIdx.x; b < f.ne; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[4 + q] += f.pe[(size_t)b * 8 + q];
+  }
+  double s[12];
+  block_sum<12>(acc, red, s);
+  if (threadIdx.x == 0) {
+    const double E_H = s[0], E_loc = s[1], E_NL = s[2];
+    const double scale = f.mode == 0 ? 1.0 : f.scale;
+    const double E_vW = s[3] * scale;
+    const double F_TF = s[4] * f.dV, E_xc = s[5] * f.dV, vn = s[6] * f.dV;
+    const double gd = s[7] * f.dV, gg = s[8] * f.dV, gpsi = s[9] * f.dV, ne = s[10] * f.dV;
+    const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + f.E_ion;
+    const double Ne = f.mode == 0 ? ne : f.Ne;
+    const double mu = (vn + E_vW) / Ne;
+    // residual^2 = (1/Q) int (g' - mu psi)^2, Q = int psi^2 (= N_e for mode 0)
+    const double Q = f.mode == 0 ? ne : f.Q;
+    const double r2 = (gg - 2.0 * mu * gpsi + mu * mu * Q) / Q;
+    double* r = f.res;
+    r[0] = F_TF; r[1] = E_vW; r[2] = E_NL; r[3] = E_H; r[4] = E_loc; r[5] = E_xc; r[6] = f.E_ion;
+    r[7] = tot; r[8] = ne; r[9] = mu; r[10] = sqrt(fmax(r2, 0.0));
+    // slope dE/dt = <g, d> with g = 2 scale (g' - mu psi_t)
+    r[11] = 2.0 * scale * (gd - mu * f.psid);
+    r[12] = vn; r[13] = s[11];
+  }
+}
+
+}  // namespace ofdft

@@ -1,0 +1,308 @@
+// Per-cell setup kernels: ion structure factor and local pseudopotential,
+// Ewald ion-ion energy, the nonlocal kernel table K(|G|), S_ei shell sums.
+#pragma once
+#include "common.cuh"
+#include "passes.cuh"
+
+namespace ofdft {
+
+// ---------------------------------------------------------------------------
+// Structure factor on the half spectrum.  Phases factorise per axis:
+// exp(-i G.R) = e_x(m_x) e_y(m_y) e_z(m_z) with e_d(m) = exp(-2 pi i m R_d / L);
+// ph[(I*3 + d)*n + k] holds them (FP64, k in FFT order).
+static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n, double L,
+                         double2* __restrict__ ph) {
+  const int tot = n_ion * 3 * n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x) {
+    const int k = q % n, d = (q / n) % 3, I = q / (3 * n);
+    const int m = k <= n / 2 - 1 ? k : k - n;
+    double f = pos[I * 3 + d] / L;
+    f -= floor(f);                       // wrap into [0, 1)
+    // angle = -2 pi m f; reduce m f modulo 1 before the trig call
+    double mf = (double)m * f;
+    mf -= rint(mf);
+    double s, c;
+    sincospi(-2.0 * mf, &s, &c);
+    ph[q] = make_double2(c, s);
+  }
+}
+
+// S(G) = sum_I exp(-i G.R_I) and S_Z(G) = sum_I Z_I exp(-i G.R_I) on the half
+// spectrum; V_loc(G) = (1/Omega) v~(G) S_Z(G) with the common smoothing radius
+// rc; the Ewald reciprocal sum (2 pi / Omega) sum_{G != 0} exp(-G^2/4eta^2)/G^2
+// |S_Z|^2 accumulated on the way.  One block per (kx, ky) row, threads over kz;
+// the (kx, ky) phase products of a chunk of ions are staged in shared memory.
+// Rows whose smallest |G|^2 exceeds g2max are written as zero (their V_loc and
+// Ewald weights are below double precision) unless full != 0.
+template <typename T>
+__global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, const double* __restrict__ Z,
+                                                int n_ion, int n, double L, double rc, double eta_ew,
+                                                double g2max, int full,
+                                                cplx<T>* __restrict__ S_out, cplx<T>* __restrict__ vloc,
+                                                double* __restrict__ ew_partial) {
+  constexpr int CH = 128;
+  __shared__ cplx<T> sxy[CH];
+  __shared__ T szz[CH];
+  __shared__ double red[32];
+  const int nh = n / 2 + 1;
+  const int kx = blockIdx.x / n, ky = blockIdx.x % n;
+  const int mx = kx <= n / 2 - 1 ? kx : kx - n;
+  const int my = ky <= n / 2 - 1 ? ky : ky - n;
+  const double tp = 2.0 * kPi / L;
+  const double Omega = L * L * L;
+  const double g2row = tp * tp * (double)(mx * mx + my * my);
+  const size_t rowoff = ((size_t)kx * n + ky) * nh;
+  double ew = 0;
+  if (!full && g2row > g2max) {
+    for (int kz = threadIdx.x; kz < nh; kz += blockDim.x) {
+      if (S_out) S_out[rowoff + kz] = mk<T>(0, 0);
+      vloc[rowoff + kz] = mk<T>(0, 0);
+    }
+  } else {
+    for (int kz0 = 0; kz0 < nh; kz0 += blockDim.x) {
+      const int kz = kz0 + threadIdx.x;
+      T sr = 0, si = 0, zr = 0, zi = 0;
+      for (int I0 = 0; I0 < n_ion; I0 += CH) {
+        const int cnt = min(CH, n_ion - I0);
+        __syncthreads();
+        for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+          const int I = I0 + c;
+          const double2 ex = ph[((size_t)I * 3 + 0) * n + kx];
+          const double2 ey = ph[((size_t)I * 3 + 1) * n + ky];
+          sxy[c] = mk<T>((T)(ex.x * ey.x - ex.y * ey.y), (T)(ex.x * ey.y + ex.y * ey.x));
+          szz[c] = (T)Z[I];
+        }
+        __syncthreads();
+        if (kz < nh) {
+          for (int c = 0; c < cnt; ++c) {
+            const double2 ezd = ph[((size_t)(I0 + c) * 3 + 2) * n + kz];
+            const T ezr = (T)ezd.x, ezi = (T)ezd.y;
+            const cplx<T> xy = sxy[c];
+            const T pr = xy.x * ezr - xy.y * ezi, pi = xy.x * ezi + xy.y * ezr;
+            sr += pr; si += pi;
+            zr += szz[c] * pr; zi += szz[c] * pi;
+          }
+        }
+      }
+      if (kz < nh) {
+        const int m2 = mx * mx + my * my + kz * kz;
+        const double G2 = tp * tp * (double)m2;
+        if (S_out) S_out[rowoff + kz] = mk<T>(sr, si);
+        double v;
+        if (m2 == 0) v = kPi * rc * rc;
+        else v = -4.0 * kPi * exp(-G2 * rc * rc / 4.0) / G2;
+        vloc[rowoff + kz] = mk<T>((T)(v * (double)zr / Omega), (T)(v * (double)zi / Omega));
+        if (m2 > 0) {
+          const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+          ew += w * 2.0 * kPi / Omega * exp(-G2 / (4.0 * eta_ew * eta_ew)) / G2 *
+                ((double)zr * (double)zr + (double)zi * (double)zi);
+        }
+      }
+    }
+  }
+  double v[1] = {ew}, out[1];
+  block_sum<1>(v, red, out);
+  if (threadIdx.x == 0) ew_partial[blockIdx.x] = out[0];
+}
+
+// ---------------------------------------------------------------------------
+// Ewald: real-space pair sum (all pairs I, J and lattice images within rcut).
+static __global__ void k_ewald_real(const double* __restrict__ pos, const double* __restrict__ Z, int n_ion,
+                             double L, double eta, double rcut, int nimg, double* __restrict__ partial) {
+  __shared__ double red[32];
+  double acc = 0;
+  const long npair = (long)n_ion * n_ion;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (long)gridDim.x * blockDim.x) {
+    const int I = (int)(p / n_ion), J = (int)(p % n_ion);
+    const double dx = pos[I * 3] - pos[J * 3], dy = pos[I * 3 + 1] - pos[J * 3 + 1],
+                 dz = pos[I * 3 + 2] - pos[J * 3 + 2];
+    for (int a = -nimg; a <= nimg; ++a)
+      for (int b = -nimg; b <= nimg; ++b)
+        for (int c = -nimg; c <= nimg; ++c) {
+          const double x = dx + a * L, y = dy + b * L, z = dz + c * L;
+          const double r = sqrt(x * x + y * y + z * z);
+          if (r > 1e-12 && r < rcut) acc += 0.5 * Z[I] * Z[J] * erfc(eta * r) / r;
+        }
+  }
+  double v[1] = {acc}, out[1];
+  block_sum<1>(v, red, out);
+  if (threadIdx.x == 0) partial[blockIdx.x] = out[0];
+}
+
+// ---------------------------------------------------------------------------
+// Nonlocal kernel table.  One thread per integer m^2 in [0, nm2).
+//   chi0(q;T) = -1/(pi^2 q) int_0^kmax k f(k) ln|(2k+q)/(2k-q)| dk
+// with f(k) = 1/(1 + exp((k^2/2 - mu0)/T)).  The 4k/q part of the logarithm
+// integrates to 4 pi^2 nbar / q exactly, so only the excess over it is
+// integrated (no cancellation when -1/chi0 is compared with q^2/(4 nbar)).
+// On the panel holding the logarithmic singularity c = q/2 the integrand is
+// written with g(k) = k f(k) as g [ln(2k+q) - 4k/q] - (g - g(c)) ln|2k-q| plus
+// g(c) int ln|2k-q| in closed form, and graded geometrically toward c; panel
+// widths stay below pi T / k_F so the Fermi edge is resolved.
+//   K(q) = [-1/chi0 - dmu0/dn - q^2/(4 nbar)] / (2 a^2 nbar^(2a-2)),  K(0) = 0.
+struct KernArgs {
+  double L, nbar, T, mu0, dmudn, alpha;
+  int nm2;
+};
+
+static __device__ __forceinline__ double occ_fd(double k, double mu0, double T) {
+  const double u = (0.5 * k * k - mu0) / T;
+  if (u > 0) { const double e = exp(-u); return e / (1.0 + e); }
+  return 1.0 / (1.0 + exp(u));
+}
+
+// 10-point Gauss-Legendre on [-1, 1]
+static __device__ __constant__ double c_glx[10] = {
+    -0.97390652851717172008, -0.86506336668898451073, -0.67940956829902440623, -0.43339539412924719080,
+    -0.14887433898163121088, 0.14887433898163121088, 0.43339539412924719080, 0.67940956829902440623,
+    0.86506336668898451073, 0.97390652851717172008};
+static __device__ __constant__ double c_glw[10] = {
+    0.06667134430868813759, 0.14945134915058059315, 0.21908636251598204400, 0.26926671930999635509,
+    0.29552422172787993740, 0.29552422172787993740, 0.26926671930999635509, 0.21908636251598204400,
+    0.14945134915058059315, 0.06667134430868813759};
+
+// Gauss-Legendre on [a, b] of g(k) [ln|(2k+q)/(2k-q)| - 4k/q], for panels that
+// do not contain q/2: x = 2k/q, 2 (atanh x - x) below 1, ln((x+1)/(x-1)) - 2x above.
+static __device__ double lind_panel_plain(double a, double b, double q, double mu0, double T) {
+  const double h = 0.5 * (b - a), m = 0.5 * (b + a);
+  double s = 0;
+#pragma unroll
+  for (int j = 0; j < 10; ++j) {
+    const double k = m + h * c_glx[j];
+    const double x = 2.0 * k / q;
+    const double e = x < 1.0 ? 2.0 * (atanh(x) - x) : log((x + 1.0) / (x - 1.0)) - 2.0 * x;
+    s += c_glw[j] * k * occ_fd(k, mu0, T) * e;
+  }
+  return s * h;
+}
+
+// Same integrand near q/2, written g [ln(2k+q) - 4k/q] - (g - g(c)) ln|2k - q|
+// (the g(c) ln|2k - q| part is added in closed form by the caller).
+static __device__ double lind_panel_split(double a, double b, double q, double c, double gc, double mu0,
+                                          double T) {
+  const double h = 0.5 * (b - a), m = 0.5 * (b + a);
+  double s = 0;
+#pragma unroll
+  for (int j = 0; j < 10; ++j) {
+    const double k = m + h * c_glx[j];
+    const double g = k * occ_fd(k, mu0, T);
+    const double d = fabs(2.0 * k - q);
+    double v = g * (log(2.0 * k + q) - 4.0 * k / q);
+    if (d > 0) v -= (g - gc) * log(d);
+    s += c_glw[j] * v;
+  }
+  return s * h;
+}
+
+static __global__ void k_kernel_table(KernArgs a, double* __restrict__ Kout) {
+  const int m2 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m2 >= a.nm2) return;
+  if (m2 == 0) { Kout[0] = 0.0; return; }
+  const double q = 2.0 * kPi / a.L * sqrt((double)m2);
+  const double T = a.T, mu0 = a.mu0;
+  const double kmax = sqrt(2.0 * fmax(mu0 + 45.0 * T, 45.0 * T));
+  const double kedge = mu0 > 0 ? sqrt(2.0 * mu0) : sqrt(2.0 * T);
+  double hmax = fmin(kmax / 16.0, 0.5 * kPi * T / fmax(kedge, sqrt(2.0 * T)));
+  const int npan = min(4096, (int)ceil(kmax / hmax));
+  const double h = kmax / npan;     // plain panel width
+  const double c = 0.5 * q;
+  const double gc = c * occ_fd(c, mu0, T);
+  // closed form of int ln|2k - q| dk: (1/2) [u ln|u| - u], u = 2k - q
+  auto F = [](double u) { return u == 0 ? 0.0 : u * log(fabs(u)) - u; };
+  double integral = 0;   // int_0^kmax k f(k) [ln|(2k+q)/(2k-q)| - 4k/q] dk
+  // graded region [ga, gb] around c (at least 2 panel widths on each side, so
+  // that every plain panel stays >= 2h away from the singularity)
+  const bool sing = c < kmax + 2.0 * h;
+  const double ga = sing ? fmax(0.0, c - 2.0 * h) : kmax;
+  const double gb = sing ? fmin(kmax, c + 2.0 * h) : kmax;
+  // plain panels on [0, ga] and [gb, kmax]
+  auto plain = [&](double a0, double b0) {
+    if (b0 <= a0) return;
+    const int np = max(1, (int)ceil((b0 - a0) / h));
+    const double hh = (b0 - a0) / np;
+    for (int p = 0; p < np; ++p) integral += lind_panel_plain(a0 + p * hh, a0 + (p + 1) * hh, q, mu0, T);
+  };
+  plain(0.0, ga);
+  plain(gb, kmax);
+  if (sing && gb > ga) {
+    // split at c (if inside), grade geometrically toward c from both ends
+    const double cl = fmin(fmax(c, ga), gb);
+    double lo = ga, hi = cl, w = hi - lo;
+    for (int lev = 0; lev < 48 && w > 1e-15 * (c + h); ++lev) {
+      const double mid = hi - 0.5 * w;
+      integral += lind_panel_split(lo, mid, q, c, gc, mu0, T);
+      lo = mid; w = hi - lo;
+    }
+    lo = cl; hi = gb; w = hi - lo;
+    for (int lev = 0; lev < 48 && w > 1e-15 * (c + h); ++lev) {
+      const double mid = lo + 0.5 * w;
+      integral += lind_panel_split(mid, hi, q, c, gc, mu0, T);
+      hi = mid; w = hi - lo;
+    }
+    integral -= gc * 0.5 * (F(2.0 * gb - q) - F(2.0 * ga - q));
+  }
+  // chi0 = -(4 nbar / q^2)(1 + eps);  -1/chi0 - q^2/(4 nbar) = -(q^2/(4 nbar)) eps / (1 + eps)
+  const double eps = integral * q / (4.0 * kPi * kPi * a.nbar);
+  const double resp_excess = -q * q / (4.0 * a.nbar) * eps / (1.0 + eps);
+  const double denom = 2.0 * a.alpha * a.alpha * pow(a.nbar, 2.0 * a.alpha - 2.0);
+  Kout[m2] = (resp_excess - a.dmudn) / denom;
+}
+
+// I_{-1/2}(eta) = int_0^inf 2 / (1 + exp(t^2 - eta)) dt, one thread, FP64.
+static __global__ void k_mean_density(double y, double T, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double eta, p;
+  fd_eta_p(y, eta, p);
+  const double tmax = sqrt(fmax(eta, 0.0) + 60.0);
+  const int npan = 400;
+  const double h = tmax / npan;
+  double s = 0;
+  for (int i = 0; i < npan; ++i) {
+    const double a = i * h, m = a + 0.5 * h;
+    for (int j = 0; j < 10; ++j) {
+      const double t = m + 0.5 * h * c_glx[j];
+      const double u = t * t - eta;
+      const double f = u > 0 ? exp(-u) / (1.0 + exp(-u)) : 1.0 / (1.0 + exp(u));
+      s += c_glw[j] * 2.0 * f;
+    }
+  }
+  const double im = s * 0.5 * h;
+  out[0] = eta;
+  out[1] = T * eta;                                                      // mu0
+  out[2] = 2.0 * kPi * kPi / (1.4142135623730950488 * sqrt(T) * im);     // dmu0/dn
+  out[3] = im;
+}
+
+// ---------------------------------------------------------------------------
+// S_ei shells: block s sums w Re[n_e(G) S*(G)] over the half-spectrum entries
+// of shell s (CSR lists built on the host; w = Hermitian weight), FP64, fixed
+// order.  out[2 s] = weighted sum, out[2 s + 1] = weighted count.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sei_shells(const cplx<T>* __restrict__ nt, const cplx<T>* __restrict__ S,
+                                                    const int* __restrict__ ptr, const long long* __restrict__ idx,
+                                                    const float* __restrict__ wgt, double scale,
+                                                    double* __restrict__ out) {
+  __shared__ double red[2 * 32];
+  const int s = blockIdx.x;
+  double acc[2] = {0, 0};
+  for (int e = ptr[s] + threadIdx.x; e < ptr[s + 1]; e += blockDim.x) {
+    const long long q = idx[e];
+    const cplx<T> a = nt[q], b = S[q];
+    const double w = (double)wgt[e];
+    acc[0] += w * ((double)a.x * (double)b.x + (double)a.y * (double)b.y) * scale;
+    acc[1] += w;
+  }
+  double o[2];
+  block_sum<2>(acc, red, o);
+  if (threadIdx.x == 0) { out[2 * s] = o[0]; out[2 * s + 1] = o[1]; }
+}
+
+static __global__ void k_sum_columns(const double* __restrict__ partial, int rows, int cols, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double s = 0;
+  for (int r = 0; r < rows; ++r) s += partial[(size_t)r * cols + c];
+  out[c] = s;
+}
+
+}  // namespace ofdft
