@@ -190,6 +190,36 @@ int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_
                      double* s_out, void* stream);
 
 /*
+ * ofdft_sei_shells_static: the same electron-ion structure factor as
+ * ofdft_sei_shells, for callers that must not allocate device memory while
+ * they run (a host code with a fixed, externally managed memory budget, an
+ * analysis hook called inside another program's time loop, or any process that
+ * forbids allocation after start-up so that nothing can fail or fragment
+ * mid-run).  The paper has no counterpart; this is a library-usage variant.
+ *
+ * It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  Its temporaries live in one fixed device array of about 2.5 MB that
+ * every GPU loading the library holds until the process exits.  That array
+ * bounds the inputs: n even, 2,3,5-smooth, 8 <= n <= 64, 1 <= n_shells <= 256;
+ * larger requests return OFDFT_ERR_INVALID with a message.
+ *
+ * Arguments (FP64, all device pointers except `stream`):
+ *   rho [n^3] density (layout as above), pos [n_ion][3] Cartesian ion
+ *   positions in bohr, L cell side, n_electrons the electron count used in the
+ *   1/sqrt(N_e N_i) normalisation; outputs q_out [n_shells] (1/bohr) and
+ *   s_out [n_shells], the k-th distinct nonzero |m|^2 shell in ascending order.
+ * The call synchronises `stream` before returning.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device (make that first call before capturing the stream into a graph).
+ * All calls share the one array: calls whose GPU work overlaps race on it and
+ * give wrong results, so serialise them.
+ */
+int ofdft_sei_shells_static(const double* rho, const double* pos, int n_ion, double L, int n,
+                            double n_electrons, int n_shells, double* q_out, double* s_out,
+                            void* stream);
+
+/*
  * Per-kernel launch statistics (tracing).  The paper reports only wall times
  * (Tables 2 and 3); these counters attribute device time to the library's own
  * kernels.  Launch counts are always kept.  With timing enabled, every launch

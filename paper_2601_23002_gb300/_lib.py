@@ -60,7 +60,7 @@ class KernelStat(ctypes.Structure):
 EXPORTS = ["ofdft_default_opts", "ofdft_default_min_opts", "ofdft_last_error", "ofdft_version",
            "ofdft_plan_create", "ofdft_plan_destroy", "ofdft_plan_bytes", "ofdft_structure_factor",
            "ofdft_energy_potential", "ofdft_minimize", "ofdft_sei_shells",
-           "ofdft_profile_enable", "ofdft_profile_read"]
+           "ofdft_profile_enable", "ofdft_profile_read", "ofdft_sei_shells_static"]
 
 _lib = None
 
@@ -96,6 +96,9 @@ def load(path: str | None = None):
     L.ofdft_minimize.restype = ctypes.c_int
     L.ofdft_sei_shells.argtypes = [vp, vp, ctypes.c_int, c_double_p, c_double_p, vp]
     L.ofdft_sei_shells.restype = ctypes.c_int
+    L.ofdft_sei_shells_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_int, vp, vp, vp]
+    L.ofdft_sei_shells_static.restype = ctypes.c_int
     L.ofdft_profile_enable.argtypes = [vp, ctypes.c_int]
     L.ofdft_profile_enable.restype = ctypes.c_int
     L.ofdft_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
