@@ -92,4 +92,154 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* scratch, doub
   __syncthreads();
 }
 
+// Per-thread accumulators.  FP64 plans add in double.  FP32 plans add in
+// float with Kahan compensation (GB300 issues FP64 at 1/58 of the FP32 rate,
+// so per-element FP64 adds would dominate an FP32 kernel); the compensated
+// float sum of a thread's few dozen terms is then combined across the block
+// and grid in double.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0, c = 0;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// Block sums of per-thread accumulators, written by thread 0 to out[].
+// For float accumulators the warp-level part runs in compensated float-float
+// arithmetic (a (hi, lo) pair per value, combined with Knuth's TwoSum) and
+// only the per-warp results are converted to double: on GB300 a handful of
+// FP64 operations per thread already cost as much as a streaming kernel.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  const float lo = a.lo + b.lo + e;
+  const float h2 = s + lo;
+  return FF{h2, lo - (h2 - s)};
+}
+__device__ __forceinline__ FF ff_from(const Acc<float>& a) {
+  const float hi = a.s - a.c;
+  return FF{hi, (a.s - hi) - a.c};
+}
+
+template <int NQ>
+__device__ __forceinline__ void block_sum_acc(Acc<double> (&a)[NQ], double* scratch, double* out) {
+  double v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = a[q].get();
+  block_sum<NQ>(v, scratch, out);
+}
+
+template <int NQ>
+__device__ __forceinline__ void block_sum_acc(Acc<float> (&a)[NQ], double* scratch, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    FF f = ff_from(a[q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      FF g;
+      g.hi = __shfl_xor_sync(0xffffffffu, f.hi, o);
+      g.lo = __shfl_xor_sync(0xffffffffu, f.lo, o);
+      f = ff_add(f, g);
+    }
+    if (lane == 0) scratch[q * 32 + wid] = (double)f.hi + (double)f.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NQ; ++q) {
+      double t = 0;
+      for (int w = 0; w < nw; ++w) t += scratch[q * 32 + w];
+      out[q] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// True in exactly one block: the last to arrive.  Every block must call it
+// (after its thread 0 has written the block's partial results); the last one
+// then reads all partials (use __ldcg) and resets the counter for the next
+// launch in the stream.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+// One block: out[c] = sum_r partial[r * cols + c], fixed order, FP64.  Thread
+// t sums column t % cols over rows t / cols, t / cols + k, ... (k = blockDim /
+// cols row groups, loads coalesced along each row); then one thread per column
+// adds the k group sums.  Requires cols <= blockDim.x.
+__device__ __forceinline__ void block_sum_columns(const double* partial, int rows, int cols, double* out,
+                                                  double* /*unused*/) {
+  __shared__ double colscr[1024];
+  const int k = blockDim.x / cols;
+  const int t = threadIdx.x;
+  double v = 0;
+  if (t < k * cols) {
+    const int c = t % cols;
+    for (int r = t / cols; r < rows; r += k) v += __ldcg(partial + (size_t)r * cols + c);
+  }
+  colscr[t] = v;
+  __syncthreads();
+  if (t < cols) {
+    double s2 = 0;
+    for (int g = 0; g < k; ++g) s2 += colscr[g * cols + t];
+    out[t] = s2;
+  }
+  __syncthreads();
+}
+
+// Block-wide sums of nq <= NQMAX per-thread accumulators in one pass: each
+// warp reduces every value (float-float for float accumulators), lane 0 parks
+// it in shared memory, then thread q < nq adds the warp results in double and
+// writes dst[q] (deterministic).
+template <int NQMAX, typename T>
+__device__ __forceinline__ void block_sum_many(const Acc<T>* a, int nq, double* dst) {
+  __shared__ double wres[32 * NQMAX];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQMAX; ++q) {
+    if (q < nq) {
+      double r;
+      if constexpr (sizeof(T) == 4) {
+        FF f = ff_from(a[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          FF g;
+          g.hi = __shfl_xor_sync(0xffffffffu, f.hi, o);
+          g.lo = __shfl_xor_sync(0xffffffffu, f.lo, o);
+          f = ff_add(f, g);
+        }
+        r = (double)f.hi + (double)f.lo;
+      } else {
+        r = warp_sum(a[q].get());
+      }
+      if (lane == 0) wres[wid * NQMAX + q] = r;
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nq) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += wres[w * NQMAX + threadIdx.x];
+    dst[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 }  // namespace ofdft

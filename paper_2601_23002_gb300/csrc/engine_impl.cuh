@@ -79,7 +79,7 @@ class Engine : public IEngine {
   // launch geometry
   int zR = 0, zP = 0, yJ = 0, xJ = 0;
   size_t smem_zf = 0, smem_zi = 0, smem_y = 0, smem_x = 0;
-  int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0;
+  int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_gram = 0, nsm = 152;
   // device memory
   std::vector<void*> allocs;
   size_t nbytes = 0;
@@ -96,6 +96,7 @@ class Engine : public IEngine {
   size_t partials_cap = 0;
   double* res_d = nullptr;
   double* res_h = nullptr;     // pinned
+  unsigned int* counters = nullptr;   // last-block arrival counters (0 between launches)
   double* pos_d = nullptr;
   double* Z_d = nullptr;
   double2* phases = nullptr;
@@ -105,8 +106,14 @@ class Engine : public IEngine {
   size_t n_vloc = 0;         // half-spectrum entries with |G|^2 <= g2cut_loc
   double mean_params[4] = {0, 0, 0, 0};
   Profiler prof;
+  struct Tune { int zR = 0, yJ = 0, xJ = 0; } tune;   // launch-shape overrides (0 = default)
 
-  explicit Engine(const CellSpec& c, int mmax) : cs(c), m_max(mmax) {}
+  explicit Engine(const CellSpec& c, int mmax) : cs(c), m_max(mmax) {
+    auto env = [](const char* k) { const char* v = std::getenv(k); return v ? std::atoi(v) : 0; };
+    tune.zR = env("OFDFT_ZR");
+    tune.yJ = env("OFDFT_YJ");
+    tune.xJ = env("OFDFT_XJ");
+  }
   ~Engine() override {
     for (void* p : allocs) cudaFree(p);
     if (res_h) cudaFreeHost(res_h);
@@ -170,10 +177,13 @@ class Engine : public IEngine {
     L = cs.L; Omega = L * L * L; dV = Omega / (double)N;
     Ne = 0; for (double z : cs.Z) Ne += z;
     nbar = Ne / Omega; Te = cs.T;
-    zR = std::max(1, std::min(32, 2048 / h));
+    zR = std::max(1, std::min(16, 1024 / h));     // 16 rows per block: best in a sweep at 128^3
     zP = nh | 1;                                  // odd row pitch >= h + 1
     yJ = sizeof(T) == 4 ? 16 : 8;
     xJ = yJ;
+    if (tune.zR > 0) zR = tune.zR;
+    if (tune.yJ > 0) yJ = tune.yJ;
+    if (tune.xJ > 0) xJ = tune.xJ;
     smem_zf = align16((size_t)zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
     smem_zi = align16((size_t)3 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
     smem_y = 2 * (size_t)n * yJ * sizeof(C);
@@ -181,7 +191,10 @@ class Engine : public IEngine {
     grid_z = (int)(((size_t)n * n + zR - 1) / zR);
     grid_y1 = n * ((nh + yJ - 1) / yJ);
     grid_x = (int)(((size_t)n * nh + xJ - 1) / xJ);
-    grid_vec = (int)std::min<size_t>(1024, (N + kThreads - 1) / kThreads);
+    // streaming vector kernels: a multiple of the SM count (4 resident blocks
+    // per SM; the Gram pass holds ~126 registers per thread, so 2)
+    grid_vec = (int)std::min<size_t>((size_t)4 * nsm, (N + kThreads - 1) / kThreads);
+    grid_gram = (int)std::min<size_t>((size_t)2 * nsm, (N + kThreads - 1) / kThreads);
   }
 
   size_t plan_bytes_estimate() {
@@ -196,6 +209,11 @@ class Engine : public IEngine {
 
   int create(void* stream_) override {
     cudaStream_t st = (cudaStream_t)stream_;
+    {
+      int dev = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (nsm < 1) nsm = 152;
+    }
     geometry();
     if (!factor_radices(n, pn.radix, &pn.npass) || !factor_radices(h, ph.radix, &ph.npass)) {
       set_error("grid size not supported by the FFT radices");
@@ -237,8 +255,10 @@ class Engine : public IEngine {
     partials_cap = std::max<size_t>({(size_t)grid_x * 4 + (size_t)grid_z * 8, (size_t)grid_vec * kMaxV * kMaxW,
                                      (size_t)n * n, (size_t)4096});
     if ((rc = alloc(&partials, partials_cap))) return rc;
-    if ((rc = alloc(&res_d, 64))) return rc;
-    OFDFT_CK(cudaMallocHost(&res_h, 64 * sizeof(double)));
+    if ((rc = alloc(&res_d, 128))) return rc;
+    if ((rc = alloc(&counters, 8))) return rc;
+    OFDFT_CK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), st));
+    OFDFT_CK(cudaMallocHost(&res_h, 128 * sizeof(double)));
     if ((rc = alloc(&pos_d, (size_t)cs.Z.size() * 3))) return rc;
     if ((rc = alloc(&Z_d, cs.Z.size()))) return rc;
     if ((rc = alloc(&phases, (size_t)cs.Z.size() * 3 * n))) return rc;
@@ -335,10 +355,10 @@ class Engine : public IEngine {
       OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, 1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
     }
     double* pe = partials + (size_t)grid_x * 4;
-    EpiArgs<T> ea{mode, rho, ps, dd, t, scale, cs.alpha, Te, cs.terms, out, pe};
-    OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     FinArgs fa{partials, sp.nact > 0 ? grid_x : 0, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mode, res_d};
-    OFDFT_RUN("k_finalize", st, (double)(grid_x * 4 + grid_z * 8) * 8, k_finalize<<<1, 256, 0, st>>>(fa));
+    const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
+    EpiArgs<T> ea{mode, rho, ps, dd, t, scale, cs.alpha, Te, cy, cs.terms, out, pe, fa, counters + 0};
+    OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 14 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaStreamSynchronize(st));
@@ -366,31 +386,30 @@ class Engine : public IEngine {
   int gram(const std::vector<const T*>& V, const std::vector<const T*>& W, std::vector<double>& out,
            cudaStream_t st) {
     const int nv = (int)V.size(), nw = (int)W.size();
+    if ((size_t)nv * nw > 104 || nw > kMaxW) { set_error("gram: too many vectors"); return OFDFT_ERR_INVALID; }
     out.assign((size_t)nv * nw, 0.0);
-    std::vector<double> host;
+    // every chunk's last block writes its columns to res_d[16 + c0 * nw ...]
     for (int c0 = 0; c0 < nv; c0 += kMaxV) {
       const int cn = std::min(kMaxV, nv - c0);
       VecList<T> vl{}; vl.nv = cn;
       for (int i = 0; i < cn; ++i) vl.v[i] = V[c0 + i];
       VecList<T> wl{}; wl.nv = nw;
       for (int j = 0; j < nw; ++j) wl.v[j] = W[j];
+      double* o = res_d + 16 + (size_t)c0 * nw;
       prof.begin("k_gram", st, (double)(cn + nw) * N * sizeof(T));
       switch (nw) {
-        case 1: k_gram<T, 1><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
-        case 2: k_gram<T, 2><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
-        case 3: k_gram<T, 3><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
-        default: k_gram<T, 4><<<grid_vec, kThreads, 0, st>>>(vl, wl, N, partials); break;
+        case 1: k_gram<T, 1><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
+        case 2: k_gram<T, 2><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
+        case 3: k_gram<T, 3><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
+        default: k_gram<T, 4><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
       }
       prof.end(st);
       OFDFT_LAUNCH_CK();
-      int rc;
-      if ((rc = sum_partials(grid_vec, cn * nw, 16, st))) return rc;
-      host.resize((size_t)cn * nw);
-      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, (size_t)cn * nw * sizeof(double), cudaMemcpyDeviceToHost, st));
-      OFDFT_CK(cudaStreamSynchronize(st));
-      for (int i = 0; i < cn; ++i)
-        for (int j = 0; j < nw; ++j) out[(size_t)(c0 + i) * nw + j] = res_h[16 + i * nw + j] * dV;
     }
+    OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, (size_t)nv * nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OFDFT_CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < nv; ++i)
+      for (int j = 0; j < nw; ++j) out[(size_t)i * nw + j] = res_h[16 + i * nw + j] * dV;
     return OFDFT_OK;
   }
 
@@ -497,38 +516,58 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
 
   Ring ring; ring.m = m;
   std::vector<double> SY((size_t)kMaxMem * kMaxMem, 0.0), YY((size_t)kMaxMem * kMaxMem, 0.0);
+  std::vector<double> Sgv(kMaxMem, 0.0), Ygv(kMaxMem, 0.0);   // <s_slot, g>, <y_slot, g> for the current g
   auto sy = [&](int a, int b) -> double& { return SY[(size_t)a * kMaxMem + b]; };
   auto yy = [&](int a, int b) -> double& { return YY[(size_t)a * kMaxMem + b]; };
+  double gg = 0;
+  {
+    std::vector<double> d0;
+    if ((rc = gram({g, psi}, {g, psi}, d0, st))) return rc;
+    gg = d0[0];
+    Qcur = d0[3];
+  }
   int new_slot = -1;
   int small = 0, it = 0;
   bool converged = false;
   for (it = 1; it <= o.max_iter; ++it) {
-    // --- one pass: V = [g, psi, S_0..S_k-1, Y_0..Y_k-1], W = [g, psi, s_new, y_new]
-    const int k = ring.count;
-    std::vector<const T*> V{g, psi};
-    for (int i = 0; i < k; ++i) V.push_back(Sh[ring.slot(i)]);
-    for (int i = 0; i < k; ++i) V.push_back(Yh[ring.slot(i)]);
-    std::vector<const T*> W{g, psi};
-    if (new_slot >= 0) { W.push_back(Sh[new_slot]); W.push_back(Yh[new_slot]); }
-    if ((rc = gram(V, W, dots, st))) return rc;
-    const int nw = (int)W.size();
-    auto dt = [&](int vi, int wj) { return dots[(size_t)vi * nw + wj]; };
-    const double gg = dt(0, 0);
-    Qcur = dt(1, 1);
-    std::vector<double> Sg(k), Yg(k);
-    for (int i = 0; i < k; ++i) { Sg[i] = dt(2 + i, 0); Yg[i] = dt(2 + k + i, 0); }
     if (new_slot >= 0) {
-      for (int i = 0; i < k; ++i) {
-        const int si = ring.slot(i);
-        sy(si, new_slot) = dt(2 + i, 3);          // <s_i, y_new>
-        sy(new_slot, si) = dt(2 + k + i, 2);      // <s_new, y_i>
-        yy(si, new_slot) = dt(2 + k + i, 3);      // <y_i, y_new>
+      // the accepted pair's own dots came from k_accept (res 120..125); the
+      // older pairs are dotted with [g, s_new, y_new] in one pass
+      std::vector<int> old;
+      for (int i = 0; i < ring.count; ++i)
+        if (ring.slot(i) != new_slot) old.push_back(ring.slot(i));
+      std::vector<double> cross;
+      if (!old.empty()) {
+        std::vector<const T*> V;
+        for (int sl : old) V.push_back(Sh[sl]);
+        for (int sl : old) V.push_back(Yh[sl]);
+        if ((rc = gram(V, {g, Sh[new_slot], Yh[new_slot]}, cross, st))) return rc;
+      } else {
+        OFDFT_CK(cudaStreamSynchronize(st));
+      }
+      const double* a = res_h + 120;
+      sy(new_slot, new_slot) = a[0] * dV;
+      yy(new_slot, new_slot) = a[1] * dV;
+      Qcur = a[2] * dV;
+      gg = a[3] * dV;
+      Sgv[new_slot] = a[4] * dV;
+      Ygv[new_slot] = a[5] * dV;
+      const int no = (int)old.size();
+      for (int i = 0; i < no; ++i) {
+        const int si = old[i];
+        Sgv[si] = cross[(size_t)i * 3 + 0];
+        sy(si, new_slot) = cross[(size_t)i * 3 + 2];            // <s_i, y_new>
+        Ygv[si] = cross[(size_t)(no + i) * 3 + 0];
+        sy(new_slot, si) = cross[(size_t)(no + i) * 3 + 1];     // <s_new, y_i>
+        yy(si, new_slot) = cross[(size_t)(no + i) * 3 + 2];     // <y_i, y_new>
         yy(new_slot, si) = yy(si, new_slot);
       }
       if (!(sy(new_slot, new_slot) > 0)) ring.clear();   // curvature lost to rounding: restart
       new_slot = -1;
     }
     const int kk = ring.count;
+    std::vector<double> Sg(kk), Yg(kk);
+    for (int i = 0; i < kk; ++i) { Sg[i] = Sgv[ring.slot(i)]; Yg[i] = Ygv[ring.slot(i)]; }
     // --- two-loop recursion carried out on the Gram scalars
     std::vector<double> alpha(kk, 0.0), beta(kk, 0.0), rho(kk, 0.0);
     for (int i = 0; i < kk; ++i) rho[i] = 1.0 / sy(ring.slot(i), ring.slot(i));
@@ -561,8 +600,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     }
     double dd = 0, dg = 0, dpsi = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-      OFDFT_RUN("k_lincomb", st, (double)(vl.nv + 3) * N * sizeof(T), k_lincomb<T><<<grid_vec, kThreads, 0, st>>>(vl, d, g, psi, N, partials));
-      if ((rc = sum_partials(grid_vec, 3, 16, st))) return rc;
+      OFDFT_RUN("k_lincomb", st, (double)(vl.nv + 3) * N * sizeof(T), k_lincomb<T><<<grid_vec, kThreads, 0, st>>>(vl, d, g, psi, N, partials, counters + 2, res_d + 16));
       OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaStreamSynchronize(st));
       dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
@@ -599,7 +637,8 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     if (rc) return rc;
     // --- accept: s = t d, y = g_t - g, psi += t d, g = g_t  (the last trial is the accepted one)
     const int slot = ring.push();
-    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, acc.t, gp, lastScale, lastMu, g, Sh[slot], Yh[slot], N));
+    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, acc.t, gp, lastScale, lastMu, g, Sh[slot], Yh[slot], N, partials, counters + 3, res_d + 120));
+    OFDFT_CK(cudaMemcpyAsync(res_h + 120, res_d + 120, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     new_slot = slot;
     const double dF = std::fabs(acc.f - F) / n_ion;
     F = acc.f;

@@ -149,10 +149,11 @@ __global__ void __launch_bounds__(256) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPl
   const size_t off = row0 * n;
   const int tot = R * n;
   // psi_t (or sqrt rho) for the block's rows
+  const T tstep = (T)a.t;
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
     T v;
     if (a.mode == 0) v = sqrt(fmax(a.rho[off + q], (T)0));
-    else v = a.psi[off + q] + (T)a.t * a.d[off + q];
+    else v = a.psi[off + q] + tstep * a.d[off + q];
     psit[q] = v;
   }
   __syncthreads();
@@ -269,8 +270,11 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
   const size_t plane = (size_t)n * nh;   // stride between consecutive kx
   const size_t j0 = (size_t)blockIdx.x * J;
   const int jn = (int)min((size_t)J, plane - j0);
-  const double twopiL = 2.0 * kPi / g.L;
-  double acc[4] = {0, 0, 0, 0};
+  // G-space arithmetic in the plan's precision (float for FP32 plans)
+  const T twopiL = (T)(2.0 * kPi / g.L);
+  const T invN = (T)g.invN, Om = (T)g.Omega, halfOm = (T)(0.5 * g.Omega), fourpi = (T)(4.0 * kPi);
+  const T g2cut = (T)g.g2cut_loc;
+  Acc<T> acc[4];
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
     cplx<T>* base = sp.s[fid] + j0;
@@ -284,36 +288,37 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
       const int kx = q / J, j = q % J;
       if (j >= jn) { F[q] = mk<T>(0, 0); continue; }
       const size_t jj = j0 + j;
-      const int ky = (int)(jj / nh), kz = (int)(jj % nh);
+      const int jl = (int)jj;                     // < n (n/2+1) <= 2^31
+      const int ky = jl / nh, kz = jl - ky * nh;
       const int mx = kx <= n / 2 - 1 ? kx : kx - n;
       const int my = ky <= n / 2 - 1 ? ky : ky - n;
       const int m2 = mx * mx + my * my + kz * kz;
-      const double G2 = twopiL * twopiL * (double)m2;
-      const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+      const T G2 = twopiL * twopiL * (T)m2;
+      const T w = (kz == 0 || 2 * kz == n) ? (T)1 : (T)2;
       const cplx<T> v = F[q];
-      const double vr = (double)v.x * g.invN, vi = (double)v.y * g.invN;   // f~(G)
-      const double a2 = vr * vr + vi * vi;
+      const T vr = v.x * invN, vi = v.y * invN;   // f~(G)
+      const T a2 = vr * vr + vi * vi;
       cplx<T> o;
       if (fid == 0) {
-        double orr = 0, oi = 0;
+        T orr = 0, oi = 0;
         if (g.hartree && m2 > 0) {
-          const double c = 4.0 * kPi / G2;
-          acc[0] += w * 0.5 * g.Omega * c * a2;
+          const T c = fourpi / G2;
+          acc[0].add(w * halfOm * c * a2);
           orr = c * vr; oi = c * vi;
         }
-        if (g.vloc && G2 <= g.g2cut_loc) {
+        if (g.vloc && G2 <= g2cut) {
           const cplx<T> vl = g.vloc[(size_t)kx * plane + jj];
-          acc[1] += w * g.Omega * (vr * (double)vl.x + vi * (double)vl.y);
-          orr += (double)vl.x; oi += (double)vl.y;
+          acc[1].add(w * Om * (vr * vl.x + vi * vl.y));
+          orr += vl.x; oi += vl.y;
         }
-        o = mk<T>((T)orr, (T)oi);
+        o = mk<T>(orr, oi);
       } else if (fid == 1) {
-        const double k = (double)g.K[m2];
-        acc[2] += w * g.Omega * k * a2;
-        o = mk<T>((T)(k * vr), (T)(k * vi));
+        const T k = g.K[m2];
+        acc[2].add(w * Om * k * a2);
+        o = mk<T>(k * vr, k * vi);
       } else {
-        acc[3] += w * 0.5 * g.Omega * G2 * a2;
-        o = mk<T>((T)(G2 * vr), (T)(G2 * vi));
+        acc[3].add(w * halfOm * G2 * a2);
+        o = mk<T>(G2 * vr, G2 * vi);
       }
       F[q] = o;
     }
@@ -327,10 +332,56 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
     __syncthreads();
   }
   double out[4];
-  block_sum<4>(acc, red, out);
+  block_sum_acc<4>(acc, red, out);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) g.partials[(size_t)blockIdx.x * 4 + q] = out[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Final reduction of one evaluation, by one block (fixed order: deterministic).
+// res[]: 0 F_TF 1 E_vW 2 E_NL 3 E_H 4 E_loc 5 E_xc 6 E_ion 7 F_total 8 N_e 9 mu
+//        10 residual 11 slope <g, d> 12 int v_rest n 13 nonfinite count
+struct FinArgs {
+  const double* pg; int ng;     // G-space partials [ng][4]
+  const double* pe; int ne;     // epilogue partials [ne][8]
+  double dV, E_ion, Ne, scale, Q;  // Q = int psi_t^2 (mode 1); scale = N_e / Q
+  double psid;                  // <psi_t, d> (mode 1)
+  int mode;
+  double* res;
+};
+
+static __device__ void finalize_eval(const FinArgs& f, double* red) {
+  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < f.ng; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += __ldcg(f.pg + (size_t)b * 4 + q);
+  }
+  for (int b = threadIdx.x; b < f.ne; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[4 + q] += __ldcg(f.pe + (size_t)b * 8 + q);
+  }
+  double s[12];
+  block_sum<12>(acc, red, s);
+  if (threadIdx.x == 0) {
+    const double E_H = s[0], E_loc = s[1], E_NL = s[2];
+    const double scale = f.mode == 0 ? 1.0 : f.scale;
+    const double E_vW = s[3] * scale;
+    const double F_TF = s[4] * f.dV, E_xc = s[5] * f.dV, vn = s[6] * f.dV;
+    const double gd = s[7] * f.dV, gg = s[8] * f.dV, gpsi = s[9] * f.dV, ne = s[10] * f.dV;
+    const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + f.E_ion;
+    const double Ne = f.mode == 0 ? ne : f.Ne;
+    const double mu = (vn + E_vW) / Ne;
+    // residual^2 = (1/Q) int (g' - mu psi)^2, Q = int psi^2 (= N_e for mode 0)
+    const double Q = f.mode == 0 ? ne : f.Q;
+    const double r2 = (gg - 2.0 * mu * gpsi + mu * mu * Q) / Q;
+    double* r = f.res;
+    r[0] = F_TF; r[1] = E_vW; r[2] = E_NL; r[3] = E_H; r[4] = E_loc; r[5] = E_xc; r[6] = f.E_ion;
+    r[7] = tot; r[8] = ne; r[9] = mu; r[10] = sqrt(fmax(r2, 0.0));
+    // slope dE/dt = <g, d> with g = 2 scale (g' - mu psi_t)
+    r[11] = 2.0 * scale * (gd - mu * f.psid);
+    r[12] = vn; r[13] = s[11];
   }
 }
 
@@ -342,9 +393,12 @@ template <typename T> struct EpiArgs {
   const T* psi;
   const T* d;
   double t, scale, alpha, T_e;
+  double cy;             // pi^2 / (sqrt2 T^(3/2)): y = cy * n
   int terms;             // OFDFT_TERM_* mask
   T* out;                // v (mode 0) or g' = psi_t v_rest + lap/2 (mode 1); may be null
   double* partials;      // [gridDim.x][8]
+  FinArgs fin;           // final reduction, done by the last block to finish
+  unsigned int* counter;
 };
 
 // smem: realf[3][R][n] (T) | buf0[R][P] | buf1[R][P]
@@ -353,7 +407,7 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
                                                   const cplx<T>* __restrict__ tw_h,
                                                   const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[8 * 32];
+  __shared__ double red[12 * 32];
   const int h = n / 2, nh = h + 1;
   T* realf = reinterpret_cast<T*>(smem_raw);
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)3 * R * n * sizeof(T) + 15) & ~(size_t)15));
@@ -377,12 +431,11 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
     }
     __syncthreads();
     cplx<T>* z = fft_smem<T, +1>(buf0, buf1, ph, 1, P, R, tw_h);
-    T* dst = realf + (size_t)fid * Rfull * n;
+    // (real pairs land as one 8- or 16-byte store: realf rows are even length)
+    cplx<T>* dst = reinterpret_cast<cplx<T>*>(realf + (size_t)fid * Rfull * n);
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
       const int r = q / h, k = q % h;
-      const cplx<T> v = z[r * P + k];
-      dst[r * n + 2 * k] = v.x;
-      dst[r * n + 2 * k + 1] = v.y;
+      dst[r * h + k] = z[r * P + k];
     }
     __syncthreads();
   }
@@ -393,9 +446,10 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
   const T* fL = realf + 2 * (size_t)Rfull * n;
   const size_t off = row0 * n;
   const T Te = (T)a.T_e;
-  const T cy = (T)(9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * pow(a.T_e, 1.5)));
+  const T cy = (T)a.cy;
   const T alpha = (T)a.alpha, nmin = (T)kNmin;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const T tstep = (T)a.t, tscale = (T)a.scale;
+  Acc<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
     T psit, nval;
@@ -403,8 +457,8 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
       nval = a.rho[off + q];
       psit = sqrt(fmax(nval, (T)0));
     } else {
-      psit = a.psi[off + q] + (T)a.t * a.d[off + q];
-      nval = (T)a.scale * psit * psit;
+      psit = a.psi[off + q] + tstep * a.d[off + q];
+      nval = tscale * psit * psit;
     }
     const T nf = fmax(nval, nmin);
     T vrest = 0;
@@ -412,89 +466,43 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
       T eta, p;
       fd_eta_p(nf * cy, eta, p);
       vrest += Te * eta;
-      acc[0] += (double)(nf * Te * (eta - p));
+      acc[0].add(nf * Te * (eta - p));
     }
     if (a.terms & 8) {              // XC
       T exc, vxc;
       pz81<T>(nf, exc, vxc);
       vrest += vxc;
-      acc[1] += (double)(nval * exc);
+      acc[1].add(nval * exc);
     }
     if (has_n) vrest += fH[q];
     if (has_na) vrest += (T)2 * alpha * pow_t<T>(nf, alpha - (T)1) * fK[q];
     const T lap = has_psi ? fL[q] : (T)0;   // -lap(psi)
-    acc[2] += (double)vrest * (double)nval;
-    acc[6] += (double)nval;
+    acc[2].add(vrest * nval);
+    acc[6].add(nval);
+    const T gp = psit * vrest + (T)0.5 * lap;
     if (a.mode == 0) {
       const T phi = fmax(psit, (T)kPhiMin);
       const T v = vrest + lap / ((T)2 * phi);
       if (a.out) a.out[off + q] = v;
       // residual pieces with psi = sqrt(rho), scale 1: g' = psi v_rest + lap/2
-      const T gp = psit * vrest + (T)0.5 * lap;
-      acc[4] += (double)gp * (double)gp;
-      acc[5] += (double)gp * (double)psit;
-      if (!isfinite((double)v)) acc[7] += 1.0;
+      if (!isfinite(v)) acc[7].add((T)1);
     } else {
-      const T gp = psit * vrest + (T)0.5 * lap;
       if (a.out) a.out[off + q] = gp;
-      acc[3] += (double)gp * (double)a.d[off + q];
-      acc[4] += (double)gp * (double)gp;
-      acc[5] += (double)gp * (double)psit;
-      if (!isfinite((double)gp)) acc[7] += 1.0;
+      acc[3].add(gp * a.d[off + q]);
+      if (!isfinite(gp)) acc[7].add((T)1);
     }
+    acc[4].add(gp * gp);
+    acc[5].add(gp * psit);
   }
   double out8[8];
-  block_sum<8>(acc, red, out8);
+  block_sum_acc<8>(acc, red, out8);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) a.partials[(size_t)blockIdx.x * 8 + q] = out8[q];
   }
-}
-
-// ---------------------------------------------------------------------------
-// One-block reduction of partial sums (fixed order: deterministic).
-// res[]: 0 F_TF 1 E_vW 2 E_NL 3 E_H 4 E_loc 5 E_xc 6 E_ion 7 F_total 8 N_e 9 mu
-//        10 residual 11 slope <g, d> 12 int v_rest n 13 nonfinite count
-struct FinArgs {
-  const double* pg; int ng;     // G-space partials [ng][4]
-  const double* pe; int ne;     // epilogue partials [ne][8]
-  double dV, E_ion, Ne, scale, Q;  // Q = int psi_t^2 (mode 1); scale = N_e / Q
-  double psid;                  // <psi_t, d> (mode 1)
-  int mode;
-  double* res;
-};
-
-static __global__ void __launch_bounds__(256) k_finalize(FinArgs f) {
-  __shared__ double red[12 * 32];
-  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < f.ng; b += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += f.pg[(size_t)b * 4 + q];
-  }
-  for (int b = threadIdx.x; b < f.ne; b += blockDim.x) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[4 + q] += f.pe[(size_t)b * 8 + q];
-  }
-  double s[12];
-  block_sum<12>(acc, red, s);
-  if (threadIdx.x == 0) {
-    const double E_H = s[0], E_loc = s[1], E_NL = s[2];
-    const double scale = f.mode == 0 ? 1.0 : f.scale;
-    const double E_vW = s[3] * scale;
-    const double F_TF = s[4] * f.dV, E_xc = s[5] * f.dV, vn = s[6] * f.dV;
-    const double gd = s[7] * f.dV, gg = s[8] * f.dV, gpsi = s[9] * f.dV, ne = s[10] * f.dV;
-    const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + f.E_ion;
-    const double Ne = f.mode == 0 ? ne : f.Ne;
-    const double mu = (vn + E_vW) / Ne;
-    // residual^2 = (1/Q) int (g' - mu psi)^2, Q = int psi^2 (= N_e for mode 0)
-    const double Q = f.mode == 0 ? ne : f.Q;
-    const double r2 = (gg - 2.0 * mu * gpsi + mu * mu * Q) / Q;
-    double* r = f.res;
-    r[0] = F_TF; r[1] = E_vW; r[2] = E_NL; r[3] = E_H; r[4] = E_loc; r[5] = E_xc; r[6] = f.E_ion;
-    r[7] = tot; r[8] = ne; r[9] = mu; r[10] = sqrt(fmax(r2, 0.0));
-    // slope dE/dt = <g, d> with g = 2 scale (g' - mu psi_t)
-    r[11] = 2.0 * scale * (gd - mu * f.psid);
-    r[12] = vn; r[13] = s[11];
+  if (arrive_last(a.counter)) {
+    finalize_eval(a.fin, red);
+    if (threadIdx.x == 0) *a.counter = 0u;
   }
 }
 

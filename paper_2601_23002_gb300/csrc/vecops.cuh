@@ -7,7 +7,7 @@ namespace ofdft {
 
 constexpr int kMaxV = 9;    // vectors per gram launch (longer lists are chunked)
 constexpr int kMaxW = 4;    // targets per gram launch
-constexpr int kMaxLin = 40; // terms of a linear combination
+constexpr int kMaxLin = 20; // terms of a linear combination (1 + 2 m, m <= 8)
 
 template <typename T> struct VecList {
   const T* v[kMaxLin];
@@ -45,91 +45,112 @@ __global__ void k_project(T* __restrict__ g, const T* __restrict__ gp, const T* 
     g[i] = a * (gp[i] - m * psi[i]);
 }
 
-// All dot products <V_i, W_j>, i < nv <= kMaxV, j < NW.  partial[block][i*NW + j].
+// All dot products <V_i, W_j>, i < nv <= kMaxV, j < NW.  Per block into
+// partial[block][i*NW + j]; the last block sums the columns into out[] in a
+// fixed order.  Products and per-thread sums in the vectors' precision
+// (compensated for float), block and grid sums in double.
 template <typename T, int NW>
-__global__ void __launch_bounds__(256) k_gram(VecList<T> V, VecList<T> W, size_t N, double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_gram(VecList<T> V, VecList<T> W, size_t N, double* __restrict__ partial,
+                                              unsigned int* __restrict__ counter, double* __restrict__ out) {
   __shared__ double red[32];
-  double acc[kMaxV][NW];
-#pragma unroll
-  for (int i = 0; i < kMaxV; ++i)
-#pragma unroll
-    for (int j = 0; j < NW; ++j) acc[i][j] = 0;
+  Acc<T> acc[kMaxV][NW];
   const int nv = V.nv;
   for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    double w[NW];
+    // issue every load of this point before any use
+    T w[NW], a[kMaxV];
 #pragma unroll
-    for (int j = 0; j < NW; ++j) w[j] = (double)W.v[j][p];
+    for (int j = 0; j < NW; ++j) w[j] = W.v[j][p];
+#pragma unroll
+    for (int i = 0; i < kMaxV; ++i) a[i] = i < nv ? V.v[i][p] : (T)0;
 #pragma unroll
     for (int i = 0; i < kMaxV; ++i) {
       if (i < nv) {
-        const double a = (double)V.v[i][p];
 #pragma unroll
-        for (int j = 0; j < NW; ++j) acc[i][j] = fma(a, w[j], acc[i][j]);
+        for (int j = 0; j < NW; ++j) acc[i][j].add(a[i] * w[j]);
       }
     }
   }
-  // block reduction one value at a time (warp shuffles, then lane 0 of each warp)
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < kMaxV; ++i) {
-    if (i >= nv) break;
-#pragma unroll
-    for (int j = 0; j < NW; ++j) {
-      double s = warp_sum(acc[i][j]);
-      __syncthreads();
-      if (lane == 0) red[wid] = s;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double t = 0;
-        for (int k = 0; k < nwarp; ++k) t += red[k];
-        partial[(size_t)blockIdx.x * (nv * NW) + i * NW + j] = t;
-      }
-    }
+  const int cols = nv * NW;
+  block_sum_many<kMaxV * NW, T>(&acc[0][0], cols, partial + (size_t)blockIdx.x * cols);
+  if (arrive_last(counter)) {
+    block_sum_columns(partial, gridDim.x, cols, out, red);
+    if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
-// out = sum_i c_i V_i; partial[block][0..2] = <out,out>, <out,A>, <out,B>
+// out = sum_i c_i V_i; the last block writes res[0..2] = <out,out>, <out,A>, <out,B>
 template <typename T>
 __global__ void __launch_bounds__(256) k_lincomb(VecList<T> V, T* __restrict__ out, const T* __restrict__ A,
-                                                 const T* __restrict__ B, size_t N, double* __restrict__ partial) {
+                                                 const T* __restrict__ B, size_t N, double* __restrict__ partial,
+                                                 unsigned int* __restrict__ counter, double* __restrict__ res) {
   __shared__ double red[3 * 32];
-  double acc[3] = {0, 0, 0};
+  Acc<T> acc[3];
   const int nv = V.nv;
+  T c[kMaxLin];
+#pragma unroll
+  for (int i = 0; i < kMaxLin; ++i) c[i] = i < nv ? (T)V.c[i] : (T)0;
   for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    double s = 0;
-    for (int i = 0; i < nv; ++i) s = fma(V.c[i], (double)V.v[i][p], s);
-    const T o = (T)s;
-    out[p] = o;
-    const double od = (double)o;
-    acc[0] = fma(od, od, acc[0]);
-    acc[1] = fma(od, (double)A[p], acc[1]);
-    acc[2] = fma(od, (double)B[p], acc[2]);
+    T x[kMaxLin];
+#pragma unroll
+    for (int i = 0; i < kMaxLin; ++i) x[i] = i < nv ? V.v[i][p] : (T)0;
+    const T av = A[p], bv = B[p];
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxLin; ++i) s = fma(c[i], x[i], s);
+    out[p] = s;
+    acc[0].add(s * s);
+    acc[1].add(s * av);
+    acc[2].add(s * bv);
   }
   double r[3];
-  block_sum<3>(acc, red, r);
+  block_sum_acc<3>(acc, red, r);
   if (threadIdx.x == 0) {
     partial[(size_t)blockIdx.x * 3 + 0] = r[0];
     partial[(size_t)blockIdx.x * 3 + 1] = r[1];
     partial[(size_t)blockIdx.x * 3 + 2] = r[2];
   }
+  if (arrive_last(counter)) {
+    block_sum_columns(partial, gridDim.x, 3, res, red);
+    if (threadIdx.x == 0) *counter = 0u;
+  }
 }
 
 // Accept a line-search step t along d:
 //   psi_t = psi + t d; g_t = 2 scale_t (gp - mu_t psi_t);
-//   s = psi_t - psi (= t d); y = g_t - g; psi <- psi_t; g <- g_t.
+//   s = psi_t - psi (= t d); y = g_t - g; psi <- psi_t; g <- g_t;
+// and, on the way, the dot products of the new pair with itself, the new
+// gradient and the new psi; the last block writes res[0..5] =
+//   <s,y>, <y,y>, <psi,psi>, <g,g>, <s,g>, <y,g>   (new psi, new g).
 template <typename T>
-__global__ void k_accept(T* __restrict__ psi, const T* __restrict__ d, double t, const T* __restrict__ gp,
-                         double scale_t, double mu_t, T* __restrict__ g, T* __restrict__ s, T* __restrict__ y,
-                         size_t N) {
+__global__ void __launch_bounds__(256) k_accept(T* __restrict__ psi, const T* __restrict__ d, double t,
+                                                const T* __restrict__ gp, double scale_t, double mu_t,
+                                                T* __restrict__ g, T* __restrict__ s, T* __restrict__ y, size_t N,
+                                                double* __restrict__ partial, unsigned int* __restrict__ counter,
+                                                double* __restrict__ res) {
+  __shared__ double red[6 * 32];
   const T tt = (T)t, a = (T)(2.0 * scale_t), m = (T)mu_t;
+  Acc<T> acc[6];
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    const T p0 = psi[i];
-    const T pt = p0 + tt * d[i];
-    const T gt = a * (gp[i] - m * pt);
-    if (s) s[i] = pt - p0;
-    if (y) y[i] = gt - g[i];
+    const T p0 = psi[i], dd = d[i], gpi = gp[i], g0 = g[i];
+    const T pt = p0 + tt * dd;
+    const T gt = a * (gpi - m * pt);
+    const T si = pt - p0, yi = gt - g0;
+    s[i] = si;
+    y[i] = yi;
     psi[i] = pt;
     g[i] = gt;
+    acc[0].add(si * yi); acc[1].add(yi * yi); acc[2].add(pt * pt);
+    acc[3].add(gt * gt); acc[4].add(si * gt); acc[5].add(yi * gt);
+  }
+  double r[6];
+  block_sum_acc<6>(acc, red, r);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) partial[(size_t)blockIdx.x * 6 + q] = r[q];
+  }
+  if (arrive_last(counter)) {
+    block_sum_columns(partial, gridDim.x, 6, res, red);
+    if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
