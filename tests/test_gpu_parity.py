@@ -193,3 +193,21 @@ def test_full_size_128_minimum_is_oracle_stationary(precision):
     assert abs(e["total"] - out["F_total"]) / cell.n_ion < tol
     assert e["residual"] < 3e-4
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_128_matches_converged_oracle(precision):
+    # the oracle's own converged minimum of the 64-H 128^3 cell (written by
+    # tests/golden/make_golden.py from oracle/ alone) against the GPU minimum
+    import json, os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_minima.json")) as f:
+        ref = json.load(f)["rand64_H_rs2_n128"]
+    cell = config_cell(2)
+    plan = og.plan_for_cell(cell, precision=precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    rho = torch.empty(cell.n ** 3, dtype=dt, device="cuda")
+    out = plan.minimize(rho, start_uniform=True, tol_F_per_ion=1e-9, tol_residual=1e-6 if precision == "fp64" else 2e-5)
+    plan.close()
+    dF = abs(out["F_total"] - ref["energies"]["total"]) / cell.n_ion
+    print(f"{precision}: |F_gpu - F_oracle|/ion = {dF:.2e}")
+    assert dF < 1e-6
