@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="also run the serving loop on this many Poisson requests (0 = skip)")
+    ap.add_argument("--batch-count", type=int, default=64)
     return ap.parse_args()
 
 
@@ -222,10 +226,73 @@ def run_ours(args, rank, world, local):
         ms64, ev64, it64, last64 = timed(p64, r64, pos64, n64)
         res["fp64"] = dict(total_ms=max_over_ranks(ms64), evals=ev64, iters=it64, steps=n64, last=last64)
         p64.close()
+    if not args.no_batched:
+        res["batched"] = run_batched(args, dev)
+    if args.serving > 0:
+        res["serving"] = run_serving(args, dev)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return cell, res
+
+
+def run_batched(args, dev):
+    """64 independent snapshots of uneven size (16-128 ions, Z in {1,3,4},
+    r_s ~ U[1,3], theta ~ U[0.1,2], 48^3-96^3): the plain path (one after
+    another on one stream) against the batched form (concurrent workers, one
+    stream each).  Plans (kernel tables) are built and tiles tuned first,
+    outside both timed regions."""
+    import torch
+    import paper_2601_23002_gb300 as og
+    from workloads import batch_cells
+    cells = batch_cells(args.batch_count)
+    plans = [og.plan_for_cell(c, precision="fp32") for c in cells]
+    for p in plans:
+        p.autotune()
+    rhos = [torch.empty(c.n ** 3, dtype=torch.float32, device=dev) for c in cells]
+    torch.cuda.synchronize(dev)
+    og.minimize_batch(plans[:4], rhos[:4], concurrency=4)          # warm-up
+    t0 = time.perf_counter()
+    seq = [p.minimize(r, start_uniform=True, tol_F_per_ion=TOL_F, tol_residual=TOL_R) for p, r in zip(plans, rhos)]
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    out = {"workload": f"{len(cells)} snapshots, 16-128 ions, Z in {{1,3,4}}, r_s U[1,3], theta U[0.1,2], "
+                       f"grids {sorted(set(c.n for c in cells))}",
+           "sequential_snapshots_per_s": len(cells) / t_seq}
+    for conc in (8, 16, 32):
+        t0 = time.perf_counter()
+        res = og.minimize_batch(plans, rhos, concurrency=conc, tol_F_per_ion=TOL_F, tol_residual=TOL_R)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        out[f"batched_c{conc}_snapshots_per_s"] = len(cells) / t
+        out[f"batched_c{conc}_converged"] = sum(r["converged"] for r in res)
+    out["speedup_best"] = max(v for k, v in out.items() if k.startswith("batched_c") and k.endswith("per_s")) \
+        / out["sequential_snapshots_per_s"]
+    out["converged_sequential"] = sum(r["converged"] for r in seq)
+    for p in plans:
+        p.close()
+    return out
+
+
+def run_serving(args, dev):
+    """Poisson request stream (8-512 ions, 32^3-160^3): sequential service rate
+    first, then the continuous-batching server at 0.5, 0.9 and 1.5 times it."""
+    import numpy as np
+    from paper_2601_23002_gb300.serving import Server, run_sequential, summarize
+    from workloads import serving_requests
+    _, cells = serving_requests(args.serving)
+    srv = Server(slots=16, precision="fp32")
+    srv.prepare(cells)
+    n_seq = min(len(cells), 40)
+    _, t_seq = run_sequential(cells[:n_seq])
+    mu = n_seq / t_seq
+    out = {"requests": len(cells), "sequential_snapshots_per_s": mu, "slots": 16}
+    for rho_f in (0.5, 0.9, 1.5):
+        rng = np.random.default_rng(7)
+        arrivals = np.cumsum(rng.exponential(1.0 / (rho_f * mu), size=len(cells)))
+        done = srv.run(arrivals, cells)
+        out[f"load_{rho_f}"] = summarize(done, srv.wall)
+    return out
 
 
 # ---------------------------------------------------------- roofline helpers
@@ -375,6 +442,10 @@ def main():
                         "evals_per_sec": world * r["evals"] / (r["total_ms"] * 1e-3),
                         "evals_per_snapshot": r["evals"] / r["steps"], "steps": r["steps"],
                         "F_total": r["last"]["F_total"]}
+    if "batched" in res:
+        line["batched"] = res["batched"]
+    if "serving" in res:
+        line["serving"] = res["serving"]
     if world == 1 and not args.no_cpu_baseline:
         fallback = int(line.get("fp64", {}).get("evals_per_snapshot", r32["evals"] / args.steps))
         line["cpu_baseline"] = cpu_baseline(cell, fallback)

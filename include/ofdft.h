@@ -190,6 +190,32 @@ int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_
                      double* s_out, void* stream);
 
 /*
+ * Batched form: minimise `count` independent snapshots (one plan each, any mix
+ * of grid sizes and precisions) concurrently.  `concurrency` host workers
+ * (>= 1) each own a CUDA stream on the plans' device and take the next plan,
+ * largest grid first, so the kernels and host round trips of different
+ * snapshots overlap on the GPU.  rhos[i] is plan i's density buffer (as in
+ * ofdft_minimize); results[i] receives its result.  Every plan must have had
+ * ofdft_structure_factor called.  Returns OFDFT_OK when every snapshot
+ * converged, OFDFT_ERR_NOT_CONVERGED when some did not (their results say
+ * which), or the first other error.  Blocks until all are done.
+ */
+int ofdft_minimize_batch(ofdft_plan* const* plans, void* const* rhos, int count, int start_uniform,
+                         const ofdft_min_opts* o, ofdft_result* results, int concurrency);
+
+/*
+ * FFT tile schedule of a plan: tile[0] = grid rows per block of the z passes,
+ * tile[1] = columns per block of the y pass, tile[2] = of the x pass (each
+ * 8..64 and within shared memory).  ofdft_autotune times a few evaluations
+ * for each candidate schedule on this plan and keeps the fastest; the choice
+ * is cached per (grid size, precision) for the process, so later plans of the
+ * same size reuse it without timing.  Requires ofdft_structure_factor first.
+ * us_per_eval (may be NULL) receives the measured evaluation time.
+ */
+int ofdft_autotune(ofdft_plan* plan, void* stream, int* tile, double* us_per_eval);
+int ofdft_set_tiles(ofdft_plan* plan, const int* tile);
+
+/*
  * ofdft_sei_shells_static: the same electron-ion structure factor as
  * ofdft_sei_shells, for callers that must not allocate device memory while
  * they run (a host code with a fixed, externally managed memory budget, an

@@ -60,7 +60,8 @@ class KernelStat(ctypes.Structure):
 EXPORTS = ["ofdft_default_opts", "ofdft_default_min_opts", "ofdft_last_error", "ofdft_version",
            "ofdft_plan_create", "ofdft_plan_destroy", "ofdft_plan_bytes", "ofdft_structure_factor",
            "ofdft_energy_potential", "ofdft_minimize", "ofdft_sei_shells",
-           "ofdft_profile_enable", "ofdft_profile_read", "ofdft_sei_shells_static"]
+           "ofdft_profile_enable", "ofdft_profile_read", "ofdft_sei_shells_static",
+           "ofdft_minimize_batch", "ofdft_autotune", "ofdft_set_tiles"]
 
 _lib = None
 
@@ -99,6 +100,13 @@ def load(path: str | None = None):
     L.ofdft_sei_shells_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_int, vp, vp, vp]
     L.ofdft_sei_shells_static.restype = ctypes.c_int
+    L.ofdft_minimize_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(MinOpts), ctypes.POINTER(Result), ctypes.c_int]
+    L.ofdft_minimize_batch.restype = ctypes.c_int
+    L.ofdft_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.ofdft_autotune.restype = ctypes.c_int
+    L.ofdft_set_tiles.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.ofdft_set_tiles.restype = ctypes.c_int
     L.ofdft_profile_enable.argtypes = [vp, ctypes.c_int]
     L.ofdft_profile_enable.restype = ctypes.c_int
     L.ofdft_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]

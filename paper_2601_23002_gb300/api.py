@@ -112,6 +112,17 @@ class Plan:
                    converged=r.status == C.OFDFT_OK)
         return out
 
+    def autotune(self):
+        """Pick the FFT tile schedule (cached per grid size and precision)."""
+        t = (ctypes.c_int * 3)()
+        us = ctypes.c_double(0)
+        _check(self.lib.ofdft_autotune(self._p, _stream_ptr(self.stream), t, ctypes.byref(us)))
+        return tuple(t), us.value
+
+    def set_tiles(self, tiles):
+        t = (ctypes.c_int * 3)(*[int(x) for x in tiles])
+        _check(self.lib.ofdft_set_tiles(self._p, t))
+
     def profile_enable(self, timing: bool = True):
         """Reset the per-kernel counters; with timing, bracket launches by events."""
         _check(self.lib.ofdft_profile_enable(self._p, int(bool(timing))))
@@ -132,6 +143,32 @@ class Plan:
                                          q.ctypes.data_as(C.c_double_p), s.ctypes.data_as(C.c_double_p),
                                          _stream_ptr(self.stream)))
         return q, s
+
+
+def minimize_batch(plans, rhos, concurrency: int = 8, start_uniform: bool = True, tol_F_per_ion: float = 1e-6,
+                   tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000, c1: float = 1e-4,
+                   c2: float = 0.9) -> list:
+    """Minimise independent snapshots concurrently (ofdft_minimize_batch).
+    Returns one result dict per plan, in order."""
+    lib = C.load()
+    cnt = len(plans)
+    for p, r in zip(plans, rhos):
+        p._field(r, "rho")
+    P = (ctypes.c_void_p * cnt)(*[p._p.value for p in plans])
+    R = (ctypes.c_void_p * cnt)(*[r.data_ptr() for r in rhos])
+    res = (C.Result * cnt)()
+    o = C.MinOpts(tol_F_per_ion, tol_residual, m, max_iter, c1, c2)
+    torch.cuda.synchronize()
+    rc = lib.ofdft_minimize_batch(P, R, cnt, int(bool(start_uniform)), ctypes.byref(o), res, int(concurrency))
+    if rc not in (C.OFDFT_OK, C.OFDFT_ERR_NOT_CONVERGED):
+        _check(rc)
+    out = []
+    for i in range(cnt):
+        d = res[i].e.as_dict()
+        d.update(iterations=res[i].iterations, evaluations=res[i].evaluations, status=res[i].status,
+                 converged=res[i].status == C.OFDFT_OK)
+        out.append(d)
+    return out
 
 
 def plan_for_cell(cell, precision="fp64", terms=C.TERMS_ALL, alpha=0.5, stream=None) -> Plan:

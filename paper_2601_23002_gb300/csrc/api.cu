@@ -1,9 +1,16 @@
 // C-ABI entry points (include/ofdft.h): argument validation, plan lifetime,
 // dispatch to the FP32 or FP64 engine.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -181,6 +188,95 @@ int ofdft_profile_enable(ofdft_plan* plan, int timing) {
 int ofdft_profile_read(ofdft_plan* plan, ofdft_kernel_stat* out, int max, int* count) {
   if (!plan || max < 0) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
   return plan->eng->profile_read(out, max, count);
+}
+
+int ofdft_minimize_batch(ofdft_plan* const* plans, void* const* rhos, int count, int start_uniform,
+                         const ofdft_min_opts* o, ofdft_result* results, int concurrency) {
+  if (count < 0 || (count > 0 && (!plans || !rhos || !results)) || concurrency < 1) {
+    set_error("ofdft_minimize_batch: bad arguments");
+    return OFDFT_ERR_INVALID;
+  }
+  for (int i = 0; i < count; ++i)
+    if (!plans[i] || !rhos[i]) { set_error("ofdft_minimize_batch: NULL plan or density"); return OFDFT_ERR_INVALID; }
+  ofdft_min_opts d;
+  ofdft_default_min_opts(&d);
+  const ofdft_min_opts oo = o ? *o : d;
+  // largest grids first
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return plans[a]->eng->grid_points() > plans[b]->eng->grid_points();
+  });
+  std::atomic<int> next{0};
+  std::vector<int> rcs(count, OFDFT_OK);
+  std::vector<std::string> errs(count);
+  const int nw = std::min(concurrency, std::max(count, 1));
+  auto worker = [&]() {
+    cudaStream_t st = nullptr;
+    int dev_cur = -1;
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = order[k];
+      if (plans[i]->device != dev_cur) {
+        if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); st = nullptr; }
+        cudaSetDevice(plans[i]->device);
+        dev_cur = plans[i]->device;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+          rcs[i] = OFDFT_ERR_CUDA;
+          errs[i] = "stream creation failed";
+          st = nullptr;
+          continue;
+        }
+      }
+      rcs[i] = plans[i]->eng->minimize(rhos[i], start_uniform, oo, &results[i], st);
+      if (rcs[i]) errs[i] = ofdft_last_error();
+    }
+    if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  int ret = OFDFT_OK;
+  for (int i = 0; i < count; ++i) {
+    if (rcs[i] && rcs[i] != OFDFT_ERR_NOT_CONVERGED) { set_error(errs[i]); return rcs[i]; }
+    if (rcs[i] == OFDFT_ERR_NOT_CONVERGED) { ret = OFDFT_ERR_NOT_CONVERGED; set_error(errs[i]); }
+  }
+  return ret;
+}
+
+static std::mutex g_tile_mu;
+static std::map<std::tuple<int, int>, std::vector<int>> g_tiles;   // (n, precision) -> tiles
+
+int ofdft_autotune(ofdft_plan* plan, void* stream, int* tile, double* us_per_eval) {
+  if (!plan) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
+  const auto key = std::make_tuple((int)std::lround(std::cbrt((double)plan->eng->grid_points())), plan->precision);
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) {
+      int rc = plan->eng->set_tiles(it->second.data());
+      if (rc == OFDFT_OK) {
+        if (tile) std::copy(it->second.begin(), it->second.end(), tile);
+        if (us_per_eval) *us_per_eval = -1.0;   // reused, not timed
+      }
+      return rc;
+    }
+  }
+  int t[3] = {0, 0, 0};
+  int rc = plan->eng->autotune(stream, t, us_per_eval);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    g_tiles[key] = std::vector<int>(t, t + 3);
+  }
+  if (tile) std::copy(t, t + 3, tile);
+  return OFDFT_OK;
+}
+
+int ofdft_set_tiles(ofdft_plan* plan, const int* tile) {
+  if (!plan || !tile) { set_error("plan and tile must not be NULL"); return OFDFT_ERR_INVALID; }
+  return plan->eng->set_tiles(tile);
 }
 
 }  // extern "C"

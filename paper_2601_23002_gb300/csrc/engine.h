@@ -29,6 +29,9 @@ class IEngine {
                        void* stream) = 0;
   virtual int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream) = 0;
   virtual size_t bytes() const = 0;
+  virtual int autotune(void* stream, int* tile, double* us_per_eval) = 0;
+  virtual int set_tiles(const int* tile) = 0;
+  virtual long long grid_points() const = 0;
   virtual int profile_enable(int timing) = 0;
   virtual int profile_read(ofdft_kernel_stat* out, int max, int* count) = 0;
 };

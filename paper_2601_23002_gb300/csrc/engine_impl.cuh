@@ -181,9 +181,11 @@ class Engine : public IEngine {
     zP = nh | 1;                                  // odd row pitch >= h + 1
     yJ = sizeof(T) == 4 ? 16 : 8;
     xJ = yJ;
-    if (tune.zR > 0) zR = tune.zR;
-    if (tune.yJ > 0) yJ = tune.yJ;
-    if (tune.xJ > 0) xJ = tune.xJ;
+    // overrides (autotuner, set_tiles, OFDFT_ZR/YJ/XJ) only within the shapes
+    // the reduction scratch was sized for: at least 8 rows / 8 columns
+    if (tune.zR >= 8 && tune.zR <= 64) zR = tune.zR;
+    if (tune.yJ >= 8 && tune.yJ <= 64) yJ = tune.yJ;
+    if (tune.xJ >= 8 && tune.xJ <= 64) xJ = tune.xJ;
     smem_zf = align16((size_t)zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
     smem_zi = align16((size_t)3 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
     smem_y = 2 * (size_t)n * yJ * sizeof(C);
@@ -252,8 +254,10 @@ class Engine : public IEngine {
     if ((rc = alloc(&Kd, nm2))) return rc;
     if ((rc = alloc(&Kt, nm2))) return rc;
     // eval uses [0, 4 grid_x) for G-space partials and [4 grid_x, 4 grid_x + 8 grid_z) for the epilogue
-    partials_cap = std::max<size_t>({(size_t)grid_x * 4 + (size_t)grid_z * 8, (size_t)grid_vec * kMaxV * kMaxW,
-                                     (size_t)n * n, (size_t)4096});
+    // (sized for the smallest tiles the autotuner may pick: 8 rows, 8 columns)
+    partials_cap = std::max<size_t>({(size_t)grid_x * 4 + (size_t)grid_z * 8,
+                                     ((size_t)n * nh + 7) / 8 * 4 + ((size_t)n * n + 7) / 8 * 8,
+                                     (size_t)grid_vec * kMaxV * kMaxW, (size_t)n * n, (size_t)4096});
     if ((rc = alloc(&partials, partials_cap))) return rc;
     if ((rc = alloc(&res_d, 128))) return rc;
     if ((rc = alloc(&counters, 8))) return rc;
@@ -264,12 +268,7 @@ class Engine : public IEngine {
     if ((rc = alloc(&phases, (size_t)cs.Z.size() * 3 * n))) return rc;
     OFDFT_CK(cudaMemcpyAsync(Z_d, cs.Z.data(), cs.Z.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     // shared-memory limits
-    OFDFT_CK(cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_zf));
-    OFDFT_CK(cudaFuncSetAttribute(k_zinv_epi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_zi));
-    OFDFT_CK(cudaFuncSetAttribute(k_ypass<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
-    OFDFT_CK(cudaFuncSetAttribute(k_ypass<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_y));
-    OFDFT_CK(cudaFuncSetAttribute(k_xgspace<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
-    OFDFT_CK(cudaFuncSetAttribute(k_xpass<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x));
+    if ((rc = raise_smem_limits())) return rc;
     // mean-density ideal gas: eta0, mu0, dmu0/dn
     const double y = 9.8696044010893586188 * nbar / (1.4142135623730950488 * pow(Te, 1.5));
     OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, 32, 0, st>>>(y, Te, res_d));
@@ -295,6 +294,107 @@ class Engine : public IEngine {
         }
     }
     OFDFT_CK(cudaStreamSynchronize(st));
+    return OFDFT_OK;
+  }
+
+  long long grid_points() const override { return (long long)N; }
+
+  bool tiles_fit(int r, int j) const {
+    const size_t lim = 227 * 1024;
+    const int P = nh | 1;
+    const size_t zf = align16((size_t)r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
+    const size_t zi = align16((size_t)3 * r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
+    const size_t yx = 2 * (size_t)n * j * sizeof(C);
+    return r >= 8 && j >= 8 && zf <= lim && zi <= lim && yx <= lim && j <= 64 && r <= 64;
+  }
+
+  // The dynamic shared-memory limit is a property of the kernel function, not
+  // of a plan, so it is raised once to the device's opt-in maximum (it bounds
+  // what a launch may request; occupancy follows what each launch asks for).
+  int raise_smem_limits() {
+    int dev = 0, lim = 0;
+    OFDFT_CK(cudaGetDevice(&dev));
+    OFDFT_CK(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    // dynamic limit = opt-in maximum minus the kernel's own static shared memory
+    auto raise = [&](const void* f, size_t need) -> int {
+      cudaFuncAttributes fa;
+      OFDFT_CK(cudaFuncGetAttributes(&fa, f));
+      const int dyn = lim - (int)fa.sharedSizeBytes;
+      if (dyn < (int)need) { set_error("grid too large for shared memory"); return OFDFT_ERR_INVALID; }
+      OFDFT_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+      return OFDFT_OK;
+    };
+    int rc;
+    if ((rc = raise((const void*)k_zfwd<T>, smem_zf))) return rc;
+    if ((rc = raise((const void*)k_zinv_epi<T>, smem_zi))) return rc;
+    if ((rc = raise((const void*)k_ypass<T, -1>, smem_y))) return rc;
+    if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
+    if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
+    if ((rc = raise((const void*)k_xpass<T, -1>, smem_x))) return rc;
+    return OFDFT_OK;
+  }
+
+  int apply_geometry() {
+    geometry();
+    return raise_smem_limits();
+  }
+
+  int set_tiles(const int* tile) override {
+    if (!tiles_fit(tile[0], tile[1]) || !tiles_fit(tile[0], tile[2])) {
+      set_error("tile shape does not fit in shared memory");
+      return OFDFT_ERR_INVALID;
+    }
+    tune.zR = tile[0]; tune.yJ = tile[1]; tune.xJ = tile[2];
+    return apply_geometry();
+  }
+
+  // Time a few evaluations (at the uniform density, all terms) for each
+  // candidate (rows per z block, y tile width, x tile width); keep the fastest.
+  int autotune(void* stream_, int* tile, double* us_per_eval) override {
+    if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_autotune"); return OFDFT_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream_;
+    OFDFT_RUN("k_fill", st, (double)N * sizeof(T), k_fill<T><<<grid_vec, kThreads, 0, st>>>(psi, (T)std::sqrt(nbar), N));
+    const double Q = Ne / nbar;
+    std::vector<int> rows{8, 16, 32}, cols{8, 16, 32};
+    const Tune saved = tune;
+    double best = 1e300;
+    int bt[3] = {0, 0, 0};
+    cudaEvent_t e0, e1;
+    OFDFT_CK(cudaEventCreate(&e0));
+    OFDFT_CK(cudaEventCreate(&e1));
+    int rc = OFDFT_OK;
+    for (int r : rows) {
+      if ((size_t)r > (size_t)n * n) continue;
+      for (int j : cols) {
+        if (!tiles_fit(r, j)) continue;
+        tune.zR = r; tune.yJ = j; tune.xJ = j;
+        if ((rc = apply_geometry())) break;
+        const int reps = 4;
+        for (int w = 0; w < 1 + reps && !rc; ++w) {
+          if (w == 1) OFDFT_CK(cudaEventRecord(e0, st));
+          rc = eval(1, nullptr, psi, psi, 0.0, Ne / Q, Q, Q, gp, st, false);
+        }
+        if (rc) break;
+        OFDFT_CK(cudaEventRecord(e1, st));
+        OFDFT_CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        OFDFT_CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double us = 1e3 * ms / reps;
+        if (us < best) { best = us; bt[0] = r; bt[1] = j; bt[2] = j; }
+      }
+      if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc || bt[0] == 0) {
+      tune = saved;
+      apply_geometry();
+      return rc ? rc : OFDFT_ERR_INVALID;
+    }
+    tune.zR = bt[0]; tune.yJ = bt[1]; tune.xJ = bt[2];
+    if ((rc = apply_geometry())) return rc;
+    if (tile) { tile[0] = bt[0]; tile[1] = bt[1]; tile[2] = bt[2]; }
+    if (us_per_eval) *us_per_eval = best;
     return OFDFT_OK;
   }
 

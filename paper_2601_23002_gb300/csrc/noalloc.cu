@@ -21,6 +21,7 @@
 // zero: every call overwrites what it reads.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -246,9 +247,22 @@ extern "C" int ofdft_sei_shells_static(const double* rho, const double* pos, int
   const int J = 8;
   const size_t smem_z = ((size_t)zR * n * sizeof(double) + 15) / 16 * 16 + 2 * (size_t)zR * zP * sizeof(double2);
   const size_t smem_t = 2 * (size_t)n * J * sizeof(double2);
-  NA_CK(cudaFuncSetAttribute(k_zfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z));
-  NA_CK(cudaFuncSetAttribute(k_ypass<double, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
-  NA_CK(cudaFuncSetAttribute(k_xpass<double, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
+  // The limit belongs to the kernel function, which the plans share: raise it
+  // to the device maximum instead of this call's size, so that no larger plan
+  // launched later finds it lowered.
+  int dev_lim = 0, dev_id = 0;
+  NA_CK(cudaGetDevice(&dev_id));
+  NA_CK(cudaDeviceGetAttribute(&dev_lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id));
+  if ((size_t)dev_lim < std::max(smem_z, smem_t) + 8192) { set_error("shared memory too small"); return OFDFT_ERR_INVALID; }
+  {
+    const void* fs[3] = {(const void*)k_zfwd<double>, (const void*)k_ypass<double, -1>,
+                         (const void*)k_xpass<double, -1>};
+    for (const void* f : fs) {
+      cudaFuncAttributes fa;
+      NA_CK(cudaFuncGetAttributes(&fa, f));
+      NA_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dev_lim - (int)fa.sharedSizeBytes));
+    }
+  }
   Spectra<double> sp{};
   sp.s[0] = spec; sp.nact = 1; sp.idx[0] = 0;
   ProArgs<double> pa{0, rho, nullptr, nullptr, 0.0, 1.0, 0.5};
