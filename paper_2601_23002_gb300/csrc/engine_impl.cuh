@@ -441,7 +441,7 @@ class Engine : public IEngine {
   // One evaluation.  mode 0: density rho; mode 1: psi + t d with scale.
   // Leaves results in res_d[0..13]; copies them to res_h when sync != 0.
   int eval(int mode, const T* rho, const T* ps, const T* dd, double t, double scale, double Q, double psid,
-           T* out, cudaStream_t st, bool sync) {
+           T* out, cudaStream_t st, bool sync, double mu_ref = 0.0) {
     Spectra<T> sp = spectra();
     ProArgs<T> pa{mode, rho, ps, dd, t, scale, cs.alpha};
     if (sp.nact > 0) {
@@ -455,9 +455,10 @@ class Engine : public IEngine {
       OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, 1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
     }
     double* pe = partials + (size_t)grid_x * 4;
-    FinArgs fa{partials, sp.nact > 0 ? grid_x : 0, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mode, res_d};
+    if (mode == 0) mu_ref = 0.0;
+    FinArgs fa{partials, sp.nact > 0 ? grid_x : 0, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, mode, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
-    EpiArgs<T> ea{mode, rho, ps, dd, t, scale, cs.alpha, Te, cy, cs.terms, out, pe, fa, counters + 0};
+    EpiArgs<T> ea{mode, rho, ps, dd, t, scale, cs.alpha, Te, cy, mu_ref, cs.terms, out, pe, fa, counters + 0};
     OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 14 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -613,6 +614,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
   std::memcpy(energies, res_h, sizeof(energies));
   if (!std::isfinite(F) || res_h[13] > 0) { set_error("non-finite energy at the starting density"); return OFDFT_ERR_NAN; }
   OFDFT_RUN("k_project", st, 3.0 * N * sizeof(T), k_project<T><<<grid_vec, kThreads, 0, st>>>(g, gp, psi, Ne / Qcur, res_h[9], N));
+  double mu_ref = res_h[9];   // reference chemical potential for g' (mu of the last accepted point)
 
   Ring ring; ring.m = m;
   std::vector<double> SY((size_t)kMaxMem * kMaxMem, 0.0), YY((size_t)kMaxMem * kMaxMem, 0.0);
@@ -716,7 +718,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     auto phi = [&](double t, double* f, double* slope) -> int {
       const double Qt = Qcur + 2.0 * t * dpsi + t * t * dd;
       const double sc = Ne / Qt;
-      int e = eval(1, nullptr, psi, d, t, sc, Qt, dpsi + t * dd, gp, st, true);
+      int e = eval(1, nullptr, psi, d, t, sc, Qt, dpsi + t * dd, gp, st, true, mu_ref);
       if (e) return e;
       ++evals;
       *f = res_h[13] > 0 ? NAN : res_h[7];
@@ -728,8 +730,25 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     LSPoint acc{};
     int lsev = 0;
     // energy noise: FP64 rounding, or FP32 terms summed in FP64
-    const double rel_noise = sizeof(T) == 4 ? 1e-7 : 1e-14;
+    const double rel_noise = sizeof(T) == 4 ? 3e-7 : 1e-14;
     rc = line_search(phi, F, dg, t0, o.c1, o.c2, 40, rel_noise, &acc, &lsev);
+    if (rc == OFDFT_ERR_NOT_CONVERGED && kk > 0) {
+      // failed along the quasi-Newton direction: drop the history and retry once
+      // along -g (scaled as a first step) before giving up
+      ring.clear();
+      VecList<T> v1{};
+      v1.nv = 1; v1.v[0] = g; v1.c[0] = -1.0;
+      OFDFT_RUN("k_lincomb", st, 4.0 * N * sizeof(T), k_lincomb<T><<<grid_vec, kThreads, 0, st>>>(v1, d, g, psi, N, partials, counters + 2, res_d + 16));
+      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+      dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
+      if (dg < 0) {
+        const double t1 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
+        int lsev2 = 0;
+        rc = line_search(phi, F, dg, t1, o.c1, o.c2, 40, rel_noise, &acc, &lsev2);
+        lsev += lsev2;
+      }
+    }
     if (trace)
       std::fprintf(stderr, "ofdft it %4d F %.12f dphi0 %.3e t %.3e ls_evals %d status %d R %.3e hist %d\n", it,
                    rc == OFDFT_OK ? acc.f : F, dg, acc.t, lsev, rc, lastE[10], ring.count);
@@ -737,9 +756,10 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     if (rc) return rc;
     // --- accept: s = t d, y = g_t - g, psi += t d, g = g_t  (the last trial is the accepted one)
     const int slot = ring.push();
-    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, acc.t, gp, lastScale, lastMu, g, Sh[slot], Yh[slot], N, partials, counters + 3, res_d + 120));
+    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, acc.t, gp, lastScale, lastMu - mu_ref, g, Sh[slot], Yh[slot], N, partials, counters + 3, res_d + 120));
     OFDFT_CK(cudaMemcpyAsync(res_h + 120, res_d + 120, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     new_slot = slot;
+    mu_ref = lastMu;
     const double dF = std::fabs(acc.f - F) / n_ion;
     F = acc.f;
     std::memcpy(energies, lastE, sizeof(energies));

@@ -348,6 +348,7 @@ struct FinArgs {
   const double* pe; int ne;     // epilogue partials [ne][8]
   double dV, E_ion, Ne, scale, Q;  // Q = int psi_t^2 (mode 1); scale = N_e / Q
   double psid;                  // <psi_t, d> (mode 1)
+  double mu_ref;                // reference subtracted from v_rest in g'
   int mode;
   double* res;
 };
@@ -373,14 +374,15 @@ static __device__ void finalize_eval(const FinArgs& f, double* red) {
     const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + f.E_ion;
     const double Ne = f.mode == 0 ? ne : f.Ne;
     const double mu = (vn + E_vW) / Ne;
-    // residual^2 = (1/Q) int (g' - mu psi)^2, Q = int psi^2 (= N_e for mode 0)
+    // residual^2 = (1/Q) int (g' - (mu - mu_ref) psi)^2, Q = int psi^2 (= N_e for mode 0)
     const double Q = f.mode == 0 ? ne : f.Q;
-    const double r2 = (gg - 2.0 * mu * gpsi + mu * mu * Q) / Q;
+    const double dm = mu - f.mu_ref;
+    const double r2 = (gg - 2.0 * dm * gpsi + dm * dm * Q) / Q;
     double* r = f.res;
     r[0] = F_TF; r[1] = E_vW; r[2] = E_NL; r[3] = E_H; r[4] = E_loc; r[5] = E_xc; r[6] = f.E_ion;
     r[7] = tot; r[8] = ne; r[9] = mu; r[10] = sqrt(fmax(r2, 0.0));
-    // slope dE/dt = <g, d> with g = 2 scale (g' - mu psi_t)
-    r[11] = 2.0 * scale * (gd - mu * f.psid);
+    // slope dE/dt = <g, d> with g = 2 scale (g' - (mu - mu_ref) psi_t)
+    r[11] = 2.0 * scale * (gd - dm * f.psid);
     r[12] = vn; r[13] = s[11];
   }
 }
@@ -394,6 +396,7 @@ template <typename T> struct EpiArgs {
   const T* d;
   double t, scale, alpha, T_e;
   double cy;             // pi^2 / (sqrt2 T^(3/2)): y = cy * n
+  double mu_ref;         // g' is formed with v_rest - mu_ref (mode 1), see FinArgs
   int terms;             // OFDFT_TERM_* mask
   T* out;                // v (mode 0) or g' = psi_t v_rest + lap/2 (mode 1); may be null
   double* partials;      // [gridDim.x][8]
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
   const T Te = (T)a.T_e;
   const T cy = (T)a.cy;
   const T alpha = (T)a.alpha, nmin = (T)kNmin;
-  const T tstep = (T)a.t, tscale = (T)a.scale;
+  const T tstep = (T)a.t, tscale = (T)a.scale, muref = (T)a.mu_ref;
   Acc<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
@@ -479,7 +482,9 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
     const T lap = has_psi ? fL[q] : (T)0;   // -lap(psi)
     acc[2].add(vrest * nval);
     acc[6].add(nval);
-    const T gp = psit * vrest + (T)0.5 * lap;
+    // g' = psi (v_rest - mu_ref) + lap/2: near convergence mu_ref is close to
+    // mu, so the projection g = 2 scale (g' - (mu - mu_ref) psi) cancels little
+    const T gp = psit * (vrest - muref) + (T)0.5 * lap;
     if (a.mode == 0) {
       const T phi = fmax(psit, (T)kPhiMin);
       const T v = vrest + lap / ((T)2 * phi);
