@@ -92,6 +92,34 @@ __device__ __forceinline__ void block_sum(double (&v)[NQ], double* scratch, doub
   __syncthreads();
 }
 
+// Asynchronous global -> shared copies (cp.async).  pred == false copies no
+// bytes and zero-fills the destination (the source pointer must still be a
+// valid address).  Copies of one thread complete in commit-group order.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+template <int B>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, bool pred) {
+  static_assert(B == 4 || B == 8 || B == 16, "cp.async size");
+  const int src = pred ? B : 0;
+  if constexpr (B == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(smem)), "l"(gmem), "n"(B),
+                 "r"(src)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// copy one complex element (8 or 16 bytes)
+template <typename C> __device__ __forceinline__ void cp_async_c(C* smem, const C* gmem, bool pred) {
+  cp_async<sizeof(C)>(smem, gmem, pred);
+}
+
 // Per-thread accumulators.  FP64 plans add in double.  FP32 plans add in
 // float with Kahan compensation (GB300 issues FP64 at 1/58 of the FP32 rate,
 // so per-element FP64 adds would dominate an FP32 kernel); the compensated

@@ -78,7 +78,7 @@ class Engine : public IEngine {
   FftPlan1 pn{}, ph{};
   // launch geometry
   int zR = 0, zP = 0, yJ = 0, xJ = 0;
-  size_t smem_zf = 0, smem_zi = 0, smem_y = 0, smem_x = 0;
+  size_t smem_zf = 0, smem_zi = 0, smem_y = 0, smem_x = 0, smem_xp = 0;
   int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_gram = 0, nsm = 152;
   // device memory
   std::vector<void*> allocs;
@@ -184,12 +184,14 @@ class Engine : public IEngine {
     // overrides (autotuner, set_tiles, OFDFT_ZR/YJ/XJ) only within the shapes
     // the reduction scratch was sized for: at least 8 rows / 8 columns
     if (tune.zR >= 8 && tune.zR <= 64) zR = tune.zR;
-    if (tune.yJ >= 8 && tune.yJ <= 64) yJ = tune.yJ;
-    if (tune.xJ >= 8 && tune.xJ <= 64) xJ = tune.xJ;
-    smem_zf = align16((size_t)zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
-    smem_zi = align16((size_t)3 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (tune.yJ >= 8 && tune.yJ <= 64 && pow2(tune.yJ)) yJ = tune.yJ;
+    if (tune.xJ >= 8 && tune.xJ <= 64 && pow2(tune.xJ)) xJ = tune.xJ;
+    smem_zf = align16((size_t)2 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
+    smem_zi = 3 * (size_t)zR * nh * sizeof(C) + 2 * (size_t)zR * zP * sizeof(C);
     smem_y = 2 * (size_t)n * yJ * sizeof(C);
-    smem_x = smem_y;
+    smem_x = 3 * (size_t)n * xJ * sizeof(C);
+    smem_xp = 2 * (size_t)n * xJ * sizeof(C);
     grid_z = (int)(((size_t)n * n + zR - 1) / zR);
     grid_y1 = n * ((nh + yJ - 1) / yJ);
     grid_x = (int)(((size_t)n * nh + xJ - 1) / xJ);
@@ -255,8 +257,8 @@ class Engine : public IEngine {
     if ((rc = alloc(&Kt, nm2))) return rc;
     // eval uses [0, 4 grid_x) for G-space partials and [4 grid_x, 4 grid_x + 8 grid_z) for the epilogue
     // (sized for the smallest tiles the autotuner may pick: 8 rows, 8 columns)
-    partials_cap = std::max<size_t>({(size_t)grid_x * 4 + (size_t)grid_z * 8,
-                                     ((size_t)n * nh + 7) / 8 * 4 + ((size_t)n * n + 7) / 8 * 8,
+    partials_cap = std::max<size_t>({(size_t)grid_x * 12 + (size_t)grid_z * 8,
+                                     ((size_t)n * nh + 7) / 8 * 12 + ((size_t)n * n + 7) / 8 * 8,
                                      (size_t)grid_vec * kMaxV * kMaxW, (size_t)n * n, (size_t)4096});
     if ((rc = alloc(&partials, partials_cap))) return rc;
     if ((rc = alloc(&res_d, 128))) return rc;
@@ -302,10 +304,10 @@ class Engine : public IEngine {
   bool tiles_fit(int r, int j) const {
     const size_t lim = 227 * 1024;
     const int P = nh | 1;
-    const size_t zf = align16((size_t)r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
-    const size_t zi = align16((size_t)3 * r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
-    const size_t yx = 2 * (size_t)n * j * sizeof(C);
-    return r >= 8 && j >= 8 && zf <= lim && zi <= lim && yx <= lim && j <= 64 && r <= 64;
+    const size_t zf = align16((size_t)2 * r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
+    const size_t zi = 3 * (size_t)r * nh * sizeof(C) + 2 * (size_t)r * P * sizeof(C);
+    const size_t yx = 3 * (size_t)n * j * sizeof(C);
+    return r >= 8 && j >= 8 && (j & (j - 1)) == 0 && zf <= lim && zi <= lim && yx <= lim && j <= 64 && r <= 64;
   }
 
   // The dynamic shared-memory limit is a property of the kernel function, not
@@ -330,7 +332,7 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_ypass<T, -1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
-    if ((rc = raise((const void*)k_xpass<T, -1>, smem_x))) return rc;
+    if ((rc = raise((const void*)k_xpass<T, -1>, smem_xp))) return rc;
     return OFDFT_OK;
   }
 
@@ -443,22 +445,24 @@ class Engine : public IEngine {
   int eval(int mode, const T* rho, const T* ps, const T* dd, double t, double scale, double Q, double psid,
            T* out, cudaStream_t st, bool sync, double mu_ref = 0.0) {
     Spectra<T> sp = spectra();
-    ProArgs<T> pa{mode, rho, ps, dd, t, scale, cs.alpha};
+    ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha};
     if (sp.nact > 0) {
       OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
       OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
     }
-    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? vloc : nullptr, Kt, L, Omega, 1.0 / (double)N, g2cut_loc,
-                (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0, partials};
+    const double tp = 2.0 * kPi / L;
+    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? vloc : nullptr, Kt, (T)(tp * tp), (T)Omega, (T)(0.5 * Omega),
+                (T)(1.0 / (double)N), (T)g2cut_loc, (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0, partials};
     if (sp.nact > 0) {
-      OFDFT_RUN("k_xgspace", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_xgspace<T><<<grid_x, kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
+      OFDFT_RUN("k_xgspace", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_xgspace<T><<<dim3(grid_x, sp.nact), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
       OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, 1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
     }
-    double* pe = partials + (size_t)grid_x * 4;
+    double* pe = partials + (size_t)grid_x * 3 * 4;      // after the x-pass partials [grid_x * nact][4]
     if (mode == 0) mu_ref = 0.0;
-    FinArgs fa{partials, sp.nact > 0 ? grid_x : 0, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, mode, res_d};
+    FinArgs fa{partials, grid_x * sp.nact, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, mode, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
-    EpiArgs<T> ea{mode, rho, ps, dd, t, scale, cs.alpha, Te, cy, mu_ref, cs.terms, out, pe, fa, counters + 0};
+    EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
+                  counters + 0};
     OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 14 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -756,7 +760,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     if (rc) return rc;
     // --- accept: s = t d, y = g_t - g, psi += t d, g = g_t  (the last trial is the accepted one)
     const int slot = ring.push();
-    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, acc.t, gp, lastScale, lastMu - mu_ref, g, Sh[slot], Yh[slot], N, partials, counters + 3, res_d + 120));
+    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, (T)acc.t, gp, (T)(2.0 * lastScale), (T)(lastMu - mu_ref), g, Sh[slot], Yh[slot], N, partials, counters + 3, res_d + 120));
     OFDFT_CK(cudaMemcpyAsync(res_h + 120, res_d + 120, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     new_slot = slot;
     mu_ref = lastMu;
@@ -845,11 +849,11 @@ int Engine<T>::sei_shells(const void* rho, int n_shells, double* q_out, double* 
   // forward transform of rho into spec[0]
   Spectra<T> sp{};
   sp.s[0] = spec[0]; sp.nact = 1; sp.idx[0] = 0;
-  ProArgs<T> pa{0, (const T*)rho, nullptr, nullptr, 0.0, 1.0, cs.alpha};
+  ProArgs<T> pa{0, (const T*)rho, nullptr, nullptr, (T)0, (T)1, (T)cs.alpha};
   const int mode = 0;
   OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
   OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
-  OFDFT_RUN("k_xpass", st, 2.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 1), kThreads, smem_x, st>>>(sp, pn, tw_n, n, xJ));
+  OFDFT_RUN("k_xpass", st, 2.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 1), kThreads, smem_xp, st>>>(sp, pn, tw_n, n, xJ));
   const double nion = (double)cs.Z.size();
   const double scale = Omega / (double)N / std::sqrt(Ne * nion);
   OFDFT_RUN("k_sei_shells", st, (double)idx.size() * (2 * sizeof(C) + 12), k_sei_shells<T><<<ns, 256, 0, st>>>(spec[0], Sg, ptr_d, idx_d, w_d, scale, out_d));

@@ -150,6 +150,15 @@ struct FftPlan1 {
   int radix[8];
 };
 
+// Exact quotient a / d for 0 <= a < 2^22 and d >= 1, given inv = 1/d in
+// float.  (a + 1/2)/d lies at least 1/(2d) from an integer; a + 1/2 is exact
+// in float and the two roundings (of 1/d and of the product) perturb the
+// quotient by at most (a/d) 2^-23 < 1/(2d).  Index arithmetic uses it instead
+// of integer division, which costs about twenty integer instructions.
+__device__ __forceinline__ int qdiv(int a, float inv) {
+  return __float2int_rz(((float)a + 0.5f) * inv);
+}
+
 // One Stockham pass of radix R over nb transforms of length n.
 // tw[t] = exp(-2 pi i t / n) for t in [0, n).
 template <typename T, int R, int DIR>
@@ -159,13 +168,15 @@ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in, cp
   const int m = n / R;
   const int items = nb * m;
   const int step = n / (Ns * R);
+  const float inb = 1.0f / (float)nb, ins = 1.0f / (float)Ns;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int b = it % nb, j = it / nb;
+    const int j = qdiv(it, inb), b = it - j * nb;
     cplx<T> v[R];
     const cplx<T>* src = in + (size_t)b * bs;
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * es];
-    const int k = j % Ns;
+    const int jq = qdiv(j, ins);
+    const int k = j - jq * Ns;
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -175,7 +186,7 @@ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in, cp
       }
     }
     Codelet<cplx<T>, R, DIR>::run(v);
-    const int base = (j / Ns) * Ns * R + k;
+    const int base = jq * Ns * R + k;
     cplx<T>* dst = out + (size_t)b * bs;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(base + r * Ns) * es] = v[r];

@@ -245,7 +245,8 @@ extern "C" int ofdft_sei_shells_static(const double* rho, const double* pos, int
   const int zR = std::max(1, std::min(32, 2048 / h));
   const int zP = nh | 1;
   const int J = 8;
-  const size_t smem_z = ((size_t)zR * n * sizeof(double) + 15) / 16 * 16 + 2 * (size_t)zR * zP * sizeof(double2);
+  // k_zfwd shared memory: two real row buffers (input and psi), then two complex FFT buffers
+  const size_t smem_z = ((size_t)2 * zR * n * sizeof(double) + 15) / 16 * 16 + 2 * (size_t)zR * zP * sizeof(double2);
   const size_t smem_t = 2 * (size_t)n * J * sizeof(double2);
   // The limit belongs to the kernel function, which the plans share: raise it
   // to the device maximum instead of this call's size, so that no larger plan

@@ -131,44 +131,54 @@ template <typename T> struct ProArgs {
   const T* rho;
   const T* psi;
   const T* d;
-  double t, scale, alpha;
+  T t, scale, alpha;   // converted on the host: no FP64 work in the kernels
 };
 
-// smem: psit[R][n] (T) | buf0[R][P] | buf1[R][P] (complex)
+// smem: psit[R][n] (T) | dbuf[R][n] (T) | buf0[R][P] | buf1[R][P] (complex)
 template <typename T>
-__global__ void __launch_bounds__(256) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPlan1 ph,
+__global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPlan1 ph,
                                               const cplx<T>* __restrict__ tw_h,
                                               const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int h = n / 2, nh = h + 1;
   T* psit = reinterpret_cast<T*>(smem_raw);
-  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)R * n * sizeof(T) + 15) & ~(size_t)15));
+  T* dbuf = psit + (size_t)R * n;
+  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)2 * R * n * sizeof(T) + 15) & ~(size_t)15));
   cplx<T>* buf1 = buf0 + (size_t)R * P;
   const size_t row0 = (size_t)blockIdx.x * R;
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
   const size_t off = row0 * n;
   const int tot = R * n;
-  // psi_t (or sqrt rho) for the block's rows
-  const T tstep = (T)a.t;
+  // all of the block's input rows in flight at once
+  const T* src0 = a.mode == 0 ? a.rho : a.psi;
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    T v;
-    if (a.mode == 0) v = sqrt(fmax(a.rho[off + q], (T)0));
-    else v = a.psi[off + q] + tstep * a.d[off + q];
-    psit[q] = v;
+    cp_async<sizeof(T)>(psit + q, src0 + off + q, true);
+    if (a.mode != 0) cp_async<sizeof(T)>(dbuf + q, a.d + off + q, true);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  // psi_t (or sqrt rho) in place; the raw density stays in dbuf for mode 0
+  const T tstep = a.t;
+  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+    const T x = psit[q];
+    if (a.mode == 0) { dbuf[q] = x; psit[q] = sqrt(fmax(x, (T)0)); }
+    else psit[q] = x + tstep * dbuf[q];
   }
   __syncthreads();
-  const T scale = (T)a.scale, alpha = (T)a.alpha, nmin = (T)kNmin;
+  const T scale = a.scale, alpha = a.alpha, nmin = (T)kNmin;
+  const float inh = 1.0f / (float)h, innh = 1.0f / (float)nh;
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
-      const int r = q / h, k = q % h;
+      const int r = qdiv(q, inh), k = q - r * h;
       T x0 = psit[r * n + 2 * k], x1 = psit[r * n + 2 * k + 1];
       if (fid == 0) {
-        if (a.mode == 0) { x0 = a.rho[off + r * n + 2 * k]; x1 = a.rho[off + r * n + 2 * k + 1]; }
+        if (a.mode == 0) { x0 = dbuf[r * n + 2 * k]; x1 = dbuf[r * n + 2 * k + 1]; }
         else { x0 = scale * x0 * x0; x1 = scale * x1 * x1; }
       } else if (fid == 1) {
         T n0, n1;
-        if (a.mode == 0) { n0 = a.rho[off + r * n + 2 * k]; n1 = a.rho[off + r * n + 2 * k + 1]; }
+        if (a.mode == 0) { n0 = dbuf[r * n + 2 * k]; n1 = dbuf[r * n + 2 * k + 1]; }
         else { n0 = scale * x0 * x0; n1 = scale * x1 * x1; }
         x0 = pow_t<T>(fmax(n0, nmin), alpha);
         x1 = pow_t<T>(fmax(n1, nmin), alpha);
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(256) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPl
     // X[k] = (Z[k] + Z*[h-k])/2 - (i/2) W^k (Z[k] - Z*[h-k]),  k = 0..h
     cplx<T>* out = sp.s[fid] + row0 * nh;
     for (int q = threadIdx.x; q < R * nh; q += blockDim.x) {
-      const int r = q / nh, k = q % nh;
+      const int r = qdiv(q, innh), k = q - r * nh;
       const cplx<T> zk = Z[r * P + (k == h ? 0 : k)];
       const cplx<T> zc = cconj(Z[r * P + (k == 0 ? 0 : h - k)]);
       const cplx<T> e = cadd(zk, zc);
@@ -199,7 +209,7 @@ __global__ void __launch_bounds__(256) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPl
 // at one x.  grid.x = n * ceil(nh / J), grid.y = active field.
 // smem: buf0[n][J] | buf1[n][J]
 template <typename T, int DIR>
-__global__ void __launch_bounds__(256) k_ypass(Spectra<T> sp, FftPlan1 pn, const cplx<T>* __restrict__ tw_n,
+__global__ void __launch_bounds__(256, 4) k_ypass(Spectra<T> sp, FftPlan1 pn, const cplx<T>* __restrict__ tw_n,
                                                int n, int J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -210,21 +220,24 @@ __global__ void __launch_bounds__(256) k_ypass(Spectra<T> sp, FftPlan1 pn, const
   const int kz0 = tz * J;
   const int jn = min(J, nh - kz0);
   cplx<T>* base = sp.s[sp.idx[blockIdx.y]] + (size_t)x * n * nh + kz0;
+  const int lgJ = __ffs(J) - 1;              // J is a power of two
   for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-    const int y = q / J, j = q % J;
-    buf0[q] = j < jn ? base[(size_t)y * nh + j] : mk<T>(0, 0);
+    const int y = q >> lgJ, j = q & (J - 1);
+    cp_async_c(buf0 + q, base + (j < jn ? (size_t)y * nh + j : 0), j < jn);
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   cplx<T>* res = fft_smem<T, DIR>(buf0, buf1, pn, J, 1, J, tw_n);
   for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-    const int y = q / J, j = q % J;
+    const int y = q >> lgJ, j = q & (J - 1);
     if (j < jn) base[(size_t)y * nh + j] = res[q];
   }
 }
 
 // FFT along x only (no G-space work), in place; used for analysis transforms.
 template <typename T, int DIR>
-__global__ void __launch_bounds__(256) k_xpass(Spectra<T> sp, FftPlan1 pn, const cplx<T>* __restrict__ tw_n,
+__global__ void __launch_bounds__(256, 4) k_xpass(Spectra<T> sp, FftPlan1 pn, const cplx<T>* __restrict__ tw_n,
                                                int n, int J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -234,14 +247,17 @@ __global__ void __launch_bounds__(256) k_xpass(Spectra<T> sp, FftPlan1 pn, const
   const size_t j0 = (size_t)blockIdx.x * J;
   const int jn = (int)min((size_t)J, plane - j0);
   cplx<T>* base = sp.s[sp.idx[blockIdx.y]] + j0;
+  const int lgJ = __ffs(J) - 1;              // J is a power of two
   for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-    const int kx = q / J, j = q % J;
-    buf0[q] = j < jn ? base[(size_t)kx * plane + j] : mk<T>(0, 0);
+    const int kx = q >> lgJ, j = q & (J - 1);
+    cp_async_c(buf0 + q, base + (j < jn ? (size_t)kx * plane + j : 0), j < jn);
   }
+  cp_async_commit();
+  cp_async_wait<0>();
   __syncthreads();
   cplx<T>* res = fft_smem<T, DIR>(buf0, buf1, pn, J, 1, J, tw_n);
   for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-    const int kx = q / J, j = q % J;
+    const int kx = q >> lgJ, j = q & (J - 1);
     if (j < jn) base[(size_t)kx * plane + j] = res[q];
   }
 }
@@ -252,13 +268,15 @@ __global__ void __launch_bounds__(256) k_xpass(Spectra<T> sp, FftPlan1 pn, const
 template <typename T> struct GArgs {
   const cplx<T>* vloc;   // V_loc(G), half spectrum (may be null: no local term)
   const T* K;            // K(m^2) table
-  double L, Omega;
-  double invN;
-  double g2cut_loc;      // V_loc negligible beyond this |G|^2
+  T tp2;                 // (2 pi / L)^2
+  T Om, halfOm, invN;    // Omega, Omega/2, 1/N
+  T g2cut_loc;           // V_loc negligible beyond this |G|^2
   int hartree;           // 1: add 4 pi n~/G^2 to the n field
-  double* partials;      // [gridDim.x][4]: E_H, E_loc, E_NL, E_vW(raw)
+  double* partials;      // [gridDim.y * gridDim.x][4]: E_H, E_loc, E_NL, E_vW(raw)
 };
 
+// One block per (tile, field): blockIdx.y indexes the active fields.
+// smem: buf0[n][J] | buf1[n][J] | vbuf[n][J] (V_loc tile, field 0 only)
 template <typename T>
 __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftPlan1 pn,
                                                  const cplx<T>* __restrict__ tw_n, int n, int J) {
@@ -266,76 +284,91 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
   __shared__ double red[4 * 32];
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* buf1 = buf0 + (size_t)n * J;
+  cplx<T>* vbuf = buf1 + (size_t)n * J;
   const int nh = n / 2 + 1;
   const size_t plane = (size_t)n * nh;   // stride between consecutive kx
   const size_t j0 = (size_t)blockIdx.x * J;
   const int jn = (int)min((size_t)J, plane - j0);
   // G-space arithmetic in the plan's precision (float for FP32 plans)
-  const T twopiL = (T)(2.0 * kPi / g.L);
-  const T invN = (T)g.invN, Om = (T)g.Omega, halfOm = (T)(0.5 * g.Omega), fourpi = (T)(4.0 * kPi);
-  const T g2cut = (T)g.g2cut_loc;
+  const T tp2 = g.tp2, invN = g.invN, Om = g.Om, halfOm = g.halfOm, fourpi = (T)(4.0 * kPi);
+  const T g2cut = g.g2cut_loc;
+  const int lgJ = __ffs(J) - 1;              // J is a power of two
+  const float innh = 1.0f / (float)nh;
+  const int fid = sp.idx[blockIdx.y];
+  const bool with_loc = fid == 0 && g.vloc != nullptr;
   Acc<T> acc[4];
-  for (int f = 0; f < sp.nact; ++f) {
-    const int fid = sp.idx[f];
-    cplx<T>* base = sp.s[fid] + j0;
-    for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-      const int kx = q / J, j = q % J;
-      buf0[q] = j < jn ? base[(size_t)kx * plane + j] : mk<T>(0, 0);
-    }
-    __syncthreads();
-    cplx<T>* F = fft_smem<T, -1>(buf0, buf1, pn, J, 1, J, tw_n);
-    for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-      const int kx = q / J, j = q % J;
-      if (j >= jn) { F[q] = mk<T>(0, 0); continue; }
-      const size_t jj = j0 + j;
-      const int jl = (int)jj;                     // < n (n/2+1) <= 2^31
-      const int ky = jl / nh, kz = jl - ky * nh;
-      const int mx = kx <= n / 2 - 1 ? kx : kx - n;
-      const int my = ky <= n / 2 - 1 ? ky : ky - n;
-      const int m2 = mx * mx + my * my + kz * kz;
-      const T G2 = twopiL * twopiL * (T)m2;
-      const T w = (kz == 0 || 2 * kz == n) ? (T)1 : (T)2;
-      const cplx<T> v = F[q];
-      const T vr = v.x * invN, vi = v.y * invN;   // f~(G)
-      const T a2 = vr * vr + vi * vi;
-      cplx<T> o;
-      if (fid == 0) {
-        T orr = 0, oi = 0;
-        if (g.hartree && m2 > 0) {
-          const T c = fourpi / G2;
-          acc[0].add(w * halfOm * c * a2);
-          orr = c * vr; oi = c * vi;
-        }
-        if (g.vloc && G2 <= g2cut) {
-          const cplx<T> vl = g.vloc[(size_t)kx * plane + jj];
-          acc[1].add(w * Om * (vr * vl.x + vi * vl.y));
-          orr += vl.x; oi += vl.y;
-        }
-        o = mk<T>(orr, oi);
-      } else if (fid == 1) {
-        const T k = g.K[m2];
-        acc[2].add(w * Om * k * a2);
-        o = mk<T>(k * vr, k * vi);
-      } else {
-        acc[3].add(w * halfOm * G2 * a2);
-        o = mk<T>(G2 * vr, G2 * vi);
+  cplx<T>* base = sp.s[fid] + j0;
+  // the block's spectrum tile and (field 0) its V_loc entries inside the cutoff, all in flight
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int kx = q >> lgJ, j = q & (J - 1);
+    const bool in = j < jn;
+    cp_async_c(buf0 + q, base + (in ? (size_t)kx * plane + j : 0), in);
+    if (with_loc) {
+      bool need = false;
+      if (in) {
+        const int jl = (int)(j0 + j);
+        const int ky = qdiv(jl, innh), kz = jl - ky * nh;
+        const int mx = kx <= n / 2 - 1 ? kx : kx - n;
+        const int my = ky <= n / 2 - 1 ? ky : ky - n;
+        need = tp2 * (T)(mx * mx + my * my + kz * kz) <= g2cut;
       }
-      F[q] = o;
+      cp_async_c(vbuf + q, g.vloc + (need ? (size_t)kx * plane + j0 + j : 0), need);
     }
-    __syncthreads();
-    cplx<T>* other = (F == buf0) ? buf1 : buf0;
-    cplx<T>* res = fft_smem<T, +1>(F, other, pn, J, 1, J, tw_n);
-    for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
-      const int kx = q / J, j = q % J;
-      if (j < jn) base[(size_t)kx * plane + j] = res[q];
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  cplx<T>* F = fft_smem<T, -1>(buf0, buf1, pn, J, 1, J, tw_n);
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int kx = q >> lgJ, j = q & (J - 1);
+    if (j >= jn) { F[q] = mk<T>(0, 0); continue; }
+    const int jl = (int)(j0 + j);                 // < n (n/2+1) <= 2^17
+    const int ky = qdiv(jl, innh), kz = jl - ky * nh;
+    const int mx = kx <= n / 2 - 1 ? kx : kx - n;
+    const int my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int m2 = mx * mx + my * my + kz * kz;
+    const T G2 = tp2 * (T)m2;
+    const T w = (kz == 0 || 2 * kz == n) ? (T)1 : (T)2;
+    const cplx<T> v = F[q];
+    const T vr = v.x * invN, vi = v.y * invN;   // f~(G)
+    const T a2 = vr * vr + vi * vi;
+    cplx<T> o;
+    if (fid == 0) {
+      T orr = 0, oi = 0;
+      if (g.hartree && m2 > 0) {
+        const T c = fourpi / G2;
+        acc[0].add(w * halfOm * c * a2);
+        orr = c * vr; oi = c * vi;
+      }
+      if (with_loc) {                           // zero beyond the cutoff
+        const cplx<T> vl = vbuf[q];
+        acc[1].add(w * Om * (vr * vl.x + vi * vl.y));
+        orr += vl.x; oi += vl.y;
+      }
+      o = mk<T>(orr, oi);
+    } else if (fid == 1) {
+      const T k = g.K[m2];
+      acc[2].add(w * Om * k * a2);
+      o = mk<T>(k * vr, k * vi);
+    } else {
+      acc[3].add(w * halfOm * G2 * a2);
+      o = mk<T>(G2 * vr, G2 * vi);
     }
-    __syncthreads();
+    F[q] = o;
+  }
+  __syncthreads();
+  cplx<T>* other = (F == buf0) ? buf1 : buf0;
+  cplx<T>* res = fft_smem<T, +1>(F, other, pn, J, 1, J, tw_n);
+  for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
+    const int kx = q >> lgJ, j = q & (J - 1);
+    if (j < jn) base[(size_t)kx * plane + j] = res[q];
   }
   double out[4];
   block_sum_acc<4>(acc, red, out);
   if (threadIdx.x == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) g.partials[(size_t)blockIdx.x * 4 + q] = out[q];
+    for (int q = 0; q < 4; ++q) g.partials[b * 4 + q] = out[q];
   }
 }
 
@@ -394,9 +427,9 @@ template <typename T> struct EpiArgs {
   const T* rho;
   const T* psi;
   const T* d;
-  double t, scale, alpha, T_e;
-  double cy;             // pi^2 / (sqrt2 T^(3/2)): y = cy * n
-  double mu_ref;         // g' is formed with v_rest - mu_ref (mode 1), see FinArgs
+  T t, scale, alpha, T_e;   // converted on the host: no FP64 work in the kernels
+  T cy;                  // pi^2 / (sqrt2 T^(3/2)): y = cy * n
+  T mu_ref;              // g' is formed with v_rest - mu_ref (mode 1), see FinArgs
   int terms;             // OFDFT_TERM_* mask
   T* out;                // v (mode 0) or g' = psi_t v_rest + lap/2 (mode 1); may be null
   double* partials;      // [gridDim.x][8]
@@ -404,63 +437,78 @@ template <typename T> struct EpiArgs {
   unsigned int* counter;
 };
 
-// smem: realf[3][R][n] (T) | buf0[R][P] | buf1[R][P]
+// smem: stg[3][R][nh] (complex; field f's real rows overwrite its own staging
+// once it has been pre-processed) | buf0[R][P] | buf1[R][P]
 template <typename T>
-__global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, FftPlan1 ph,
-                                                  const cplx<T>* __restrict__ tw_h,
-                                                  const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
+__global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, FftPlan1 ph,
+                                                     const cplx<T>* __restrict__ tw_h,
+                                                     const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[12 * 32];
   const int h = n / 2, nh = h + 1;
-  T* realf = reinterpret_cast<T*>(smem_raw);
-  cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)3 * R * n * sizeof(T) + 15) & ~(size_t)15));
+  cplx<T>* stg = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* buf0 = stg + (size_t)3 * R * nh;
   cplx<T>* buf1 = buf0 + (size_t)R * P;
-  // (realf is laid out for the full R rows; a short last block uses a prefix)
   const size_t row0 = (size_t)blockIdx.x * R;
   const int Rfull = R;
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
   const int tot = R * n;
+  const size_t off = row0 * n;
+  const float inh = 1.0f / (float)h;
+  // all spectrum rows of the block in flight at once (contiguous per field)
+  for (int f = 0; f < sp.nact; ++f) {
+    const cplx<T>* in = sp.s[sp.idx[f]] + row0 * nh;
+    cplx<T>* dst = stg + (size_t)f * Rfull * nh;
+    for (int q = threadIdx.x; q < R * nh; q += blockDim.x) cp_async_c(dst + q, in + q, true);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  // realf of field f = the first R*n reals of its staging slot
+  T* realf[3];
+  for (int f = 0; f < 3; ++f) realf[f] = nullptr;
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
-    const cplx<T>* in = sp.s[fid] + row0 * nh;
+    cplx<T>* in = stg + (size_t)f * Rfull * nh;
     // Z[k] = (X[k] + X*[h-k]) + i W^-k (X[k] - X*[h-k]),  k = 0..h-1
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
-      const int r = q / h, k = q % h;
-      const cplx<T> xk = in[(size_t)r * nh + k];
-      const cplx<T> xc = cconj(in[(size_t)r * nh + (h - k)]);
+      const int r = qdiv(q, inh), k = q - r * h;
+      const cplx<T> xk = in[r * nh + k];
+      const cplx<T> xc = cconj(in[r * nh + (h - k)]);
       const cplx<T> e = cadd(xk, xc);
       const cplx<T> o = cmul(cconj(tw_n[k]), csub(xk, xc));
       buf0[r * P + k] = mk<T>(e.x - o.y, e.y + o.x);   // e + i o
     }
-    __syncthreads();
+    __syncthreads();                                   // staging slot f is now free
     cplx<T>* z = fft_smem<T, +1>(buf0, buf1, ph, 1, P, R, tw_h);
-    // (real pairs land as one 8- or 16-byte store: realf rows are even length)
-    cplx<T>* dst = reinterpret_cast<cplx<T>*>(realf + (size_t)fid * Rfull * n);
+    // real pairs land as one 8- or 16-byte store (R h complex <= R nh slots)
+    cplx<T>* dst = in;
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
-      const int r = q / h, k = q % h;
+      const int r = qdiv(q, inh), k = q - r * h;
       dst[r * h + k] = z[r * P + k];
     }
+    realf[fid] = reinterpret_cast<T*>(in);
     __syncthreads();
   }
   // pointwise functional
   const bool has_n = sp.s[0] != nullptr, has_na = sp.s[1] != nullptr, has_psi = sp.s[2] != nullptr;
-  const T* fH = realf;
-  const T* fK = realf + (size_t)Rfull * n;
-  const T* fL = realf + 2 * (size_t)Rfull * n;
-  const size_t off = row0 * n;
-  const T Te = (T)a.T_e;
-  const T cy = (T)a.cy;
-  const T alpha = (T)a.alpha, nmin = (T)kNmin;
-  const T tstep = (T)a.t, tscale = (T)a.scale, muref = (T)a.mu_ref;
+  const T* fH = realf[0];
+  const T* fK = realf[1];
+  const T* fL = realf[2];
+  const T Te = a.T_e;
+  const T cy = a.cy;
+  const T alpha = a.alpha, nmin = (T)kNmin;
+  const T tstep = a.t, tscale = a.scale, muref = a.mu_ref;
   Acc<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    T psit, nval;
+    T psit, nval, dq = 0;
     if (a.mode == 0) {
       nval = a.rho[off + q];
       psit = sqrt(fmax(nval, (T)0));
     } else {
-      psit = a.psi[off + q] + tstep * a.d[off + q];
+      dq = a.d[off + q];
+      psit = a.psi[off + q] + tstep * dq;
       nval = tscale * psit * psit;
     }
     const T nf = fmax(nval, nmin);
@@ -493,7 +541,7 @@ __global__ void __launch_bounds__(256) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, F
       if (!isfinite(v)) acc[7].add((T)1);
     } else {
       if (a.out) a.out[off + q] = gp;
-      acc[3].add(gp * a.d[off + q]);
+      acc[3].add(gp * dq);
       if (!isfinite(gp)) acc[7].add((T)1);
     }
     acc[4].add(gp * gp);
