@@ -195,6 +195,21 @@ __device__ __forceinline__ void block_sum_acc(Acc<float> (&a)[NQ], double* scrat
   __syncthreads();
 }
 
+// Short per-thread sums (a thread adds at most a few dozen terms): plain
+// accumulation in the plan's precision, converted to the compensated form
+// for the block reduction.
+template <typename T> struct AccShort {
+  T s = 0;
+  __device__ __forceinline__ void add(T x) { s += x; }
+};
+template <int NQ, typename T>
+__device__ __forceinline__ void block_sum_short(AccShort<T> (&a)[NQ], double* scratch, double* out) {
+  Acc<T> b[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { b[q].s = a[q].s; if constexpr (sizeof(T) == 4) b[q].c = 0; }
+  block_sum_acc<NQ>(b, scratch, out);
+}
+
 // True in exactly one block: the last to arrive.  Every block must call it
 // (after its thread 0 has written the block's partial results); the last one
 // then reads all partials (use __ldcg) and resets the counter for the next

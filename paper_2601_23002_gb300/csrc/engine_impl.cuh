@@ -157,10 +157,14 @@ class Engine : public IEngine {
   bool use_na() const { return (cs.terms & OFDFT_TERM_NL) != 0; }
   bool use_psi() const { return (cs.terms & OFDFT_TERM_VW) != 0; }
 
+  // a = 1/2 with vW and NL both on: one psi spectrum serves both terms
+  bool merged() const { return use_na() && use_psi() && cs.alpha == 0.5; }
+
   Spectra<T> spectra() const {
     Spectra<T> s{};
     s.nact = 0;
-    const bool on[3] = {use_n(), use_na(), use_psi()};
+    s.merged = merged() ? 1 : 0;
+    const bool on[3] = {use_n(), use_na() && !merged(), use_psi()};
     for (int f = 0; f < 3; ++f) {
       s.s[f] = on[f] ? spec[f] : nullptr;
       if (on[f]) s.idx[s.nact++] = f;
@@ -459,7 +463,7 @@ class Engine : public IEngine {
     }
     double* pe = partials + (size_t)grid_x * 3 * 4;      // after the x-pass partials [grid_x * nact][4]
     if (mode == 0) mu_ref = 0.0;
-    FinArgs fa{partials, grid_x * sp.nact, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, mode, res_d};
+    FinArgs fa{partials, grid_x * sp.nact, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, sp.merged, mode, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
     EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
                   counters + 0};

@@ -150,13 +150,16 @@ struct FftPlan1 {
   int radix[8];
 };
 
-// Exact quotient a / d for 0 <= a < 2^22 and d >= 1, given inv = 1/d in
-// float.  (a + 1/2)/d lies at least 1/(2d) from an integer; a + 1/2 is exact
-// in float and the two roundings (of 1/d and of the product) perturb the
-// quotient by at most (a/d) 2^-23 < 1/(2d).  Index arithmetic uses it instead
-// of integer division, which costs about twenty integer instructions.
-__device__ __forceinline__ int qdiv(int a, float inv) {
-  return __float2int_rz(((float)a + 0.5f) * inv);
+// Exact quotient a / d by one multiply-high: with M = ceil(2^32 / d),
+// floor(a M / 2^32) = floor(a/d + e) where 0 <= e < a / 2^32, and a/d is at
+// least 1/d below the next integer, so the result is exact whenever
+// a d < 2^32 (here a < 2^17 and d < 2^10).  d = 1 gives M = 0 and is handled
+// by the caller's select.  Integer division would cost about twenty
+// instructions; a float reciprocal needs conversions, which GB300 issues on
+// its narrow FP64 pipe.
+__device__ __forceinline__ unsigned qmagic(unsigned d) { return d > 1 ? 0xFFFFFFFFu / d + 1u : 0u; }
+__device__ __forceinline__ int qdiv(int a, unsigned d, unsigned M) {
+  return d > 1 ? (int)__umulhi((unsigned)a, M) : a;
 }
 
 // One Stockham pass of radix R over nb transforms of length n.
@@ -168,14 +171,14 @@ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ in, cp
   const int m = n / R;
   const int items = nb * m;
   const int step = n / (Ns * R);
-  const float inb = 1.0f / (float)nb, ins = 1.0f / (float)Ns;
+  const unsigned Mnb = qmagic(nb), Mns = qmagic(Ns);
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int j = qdiv(it, inb), b = it - j * nb;
+    const int j = qdiv(it, nb, Mnb), b = it - j * nb;
     cplx<T> v[R];
     const cplx<T>* src = in + (size_t)b * bs;
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * m) * es];
-    const int jq = qdiv(j, ins);
+    const int jq = qdiv(j, Ns, Mns);
     const int k = j - jq * Ns;
     if (Ns > 1) {
 #pragma unroll

@@ -30,6 +30,10 @@ template <typename T> struct Spectra {
   cplx<T>* s[3];    // by field index 0 = n, 1 = n^a, 2 = psi
   int nact;         // number of active fields
   int idx[3];       // active field indices, in order
+  // merged = 1 when a = 1/2 with both vW and NL on: n^(1/2) = sqrt(scale) psi,
+  // so field 2 carries both terms: W = IFFT[(K + G^2/2) psi~] and
+  // psi v_NL + (-lap psi)/2 = W (for psi >= 0); field 1 is not used
+  int merged;
 };
 
 // ---------------------------------------------------------------------------
@@ -66,7 +70,7 @@ static __device__ __forceinline__ void fd_eta_p(double y, double& eta, double& p
 }
 
 static __device__ __forceinline__ void fd_eta_p(float y, float& eta, float& p) {
-  const float s = logf(y);
+  const float s = __logf(y);      // a few ulp: far below the fit's use of s
   const float lngamma32 = -0.120782237635245222f;
   if (s < (float)FD_S_LO) {
     const float u = y * 1.12837916709551257f;
@@ -120,6 +124,31 @@ __device__ __forceinline__ void pz81(T n, T& exc, T& vxc) {
   vxc = vx + vc;
 }
 
+// FP32 plans: n^(1/3) from exp2/log2 and reciprocal multiplies (a few ulp,
+// inside float rounding of the terms they feed)
+template <>
+__device__ __forceinline__ void pz81<float>(float n, float& exc, float& vxc) {
+  const float cbn = exp2f(log2f(n) * (1.0f / 3.0f));
+  const float rs = 0.620350490899400017f * __frcp_rn(cbn);
+  const float ex = -0.738558766382022406f * cbn;
+  const float vx = (4.0f / 3.0f) * ex;
+  float ec, vc;
+  if (rs >= 1.0f) {
+    const float g = -0.1423f, b1 = 1.0529f, b2 = 0.3334f;
+    const float sq = sqrtf(rs);
+    const float inv = __frcp_rn(1.0f + b1 * sq + b2 * rs);
+    ec = g * inv;
+    vc = ec * (1.0f + (7.0f / 6.0f) * b1 * sq + (4.0f / 3.0f) * b2 * rs) * inv;
+  } else {
+    const float A = 0.0311f, B = -0.048f, C = 0.0020f, D = -0.0116f;
+    const float ln = __logf(rs);
+    ec = A * ln + B + C * rs * ln + D * rs;
+    vc = A * ln + (B - A * (1.0f / 3.0f)) + (2.0f / 3.0f) * C * rs * ln + (2.0f * D - C) * (1.0f / 3.0f) * rs;
+  }
+  exc = ex + ec;
+  vxc = vx + vc;
+}
+
 template <typename T> __device__ __forceinline__ T pow_t(T a, T b);
 template <> __device__ __forceinline__ double pow_t<double>(double a, double b) { return pow(a, b); }
 template <> __device__ __forceinline__ float pow_t<float>(float a, float b) { return exp2f(b * log2f(a)); }
@@ -167,11 +196,11 @@ __global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, Ff
   }
   __syncthreads();
   const T scale = a.scale, alpha = a.alpha, nmin = (T)kNmin;
-  const float inh = 1.0f / (float)h, innh = 1.0f / (float)nh;
+  const unsigned Mh = qmagic(h), Mnh = qmagic(nh);
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
-      const int r = qdiv(q, inh), k = q - r * h;
+      const int r = qdiv(q, h, Mh), k = q - r * h;
       T x0 = psit[r * n + 2 * k], x1 = psit[r * n + 2 * k + 1];
       if (fid == 0) {
         if (a.mode == 0) { x0 = dbuf[r * n + 2 * k]; x1 = dbuf[r * n + 2 * k + 1]; }
@@ -190,7 +219,7 @@ __global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, Ff
     // X[k] = (Z[k] + Z*[h-k])/2 - (i/2) W^k (Z[k] - Z*[h-k]),  k = 0..h
     cplx<T>* out = sp.s[fid] + row0 * nh;
     for (int q = threadIdx.x; q < R * nh; q += blockDim.x) {
-      const int r = qdiv(q, innh), k = q - r * nh;
+      const int r = qdiv(q, nh, Mnh), k = q - r * nh;
       const cplx<T> zk = Z[r * P + (k == h ? 0 : k)];
       const cplx<T> zc = cconj(Z[r * P + (k == 0 ? 0 : h - k)]);
       const cplx<T> e = cadd(zk, zc);
@@ -293,10 +322,10 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
   const T tp2 = g.tp2, invN = g.invN, Om = g.Om, halfOm = g.halfOm, fourpi = (T)(4.0 * kPi);
   const T g2cut = g.g2cut_loc;
   const int lgJ = __ffs(J) - 1;              // J is a power of two
-  const float innh = 1.0f / (float)nh;
+  const unsigned Mnh = qmagic(nh);
   const int fid = sp.idx[blockIdx.y];
   const bool with_loc = fid == 0 && g.vloc != nullptr;
-  Acc<T> acc[4];
+  AccShort<T> acc[4];
   cplx<T>* base = sp.s[fid] + j0;
   // the block's spectrum tile and (field 0) its V_loc entries inside the cutoff, all in flight
   for (int q = threadIdx.x; q < n * J; q += blockDim.x) {
@@ -307,7 +336,7 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
       bool need = false;
       if (in) {
         const int jl = (int)(j0 + j);
-        const int ky = qdiv(jl, innh), kz = jl - ky * nh;
+        const int ky = qdiv(jl, nh, Mnh), kz = jl - ky * nh;
         const int mx = kx <= n / 2 - 1 ? kx : kx - n;
         const int my = ky <= n / 2 - 1 ? ky : ky - n;
         need = tp2 * (T)(mx * mx + my * my + kz * kz) <= g2cut;
@@ -323,7 +352,7 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
     const int kx = q >> lgJ, j = q & (J - 1);
     if (j >= jn) { F[q] = mk<T>(0, 0); continue; }
     const int jl = (int)(j0 + j);                 // < n (n/2+1) <= 2^17
-    const int ky = qdiv(jl, innh), kz = jl - ky * nh;
+    const int ky = qdiv(jl, nh, Mnh), kz = jl - ky * nh;
     const int mx = kx <= n / 2 - 1 ? kx : kx - n;
     const int my = ky <= n / 2 - 1 ? ky : ky - n;
     const int m2 = mx * mx + my * my + kz * kz;
@@ -352,7 +381,14 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
       o = mk<T>(k * vr, k * vi);
     } else {
       acc[3].add(w * halfOm * G2 * a2);
-      o = mk<T>(G2 * vr, G2 * vi);
+      if (sp.merged) {
+        const T k = g.K[m2];
+        acc[2].add(w * Om * k * a2);
+        const T c = k + (T)0.5 * G2;
+        o = mk<T>(c * vr, c * vi);
+      } else {
+        o = mk<T>(G2 * vr, G2 * vi);
+      }
     }
     F[q] = o;
   }
@@ -364,7 +400,7 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
     if (j < jn) base[(size_t)kx * plane + j] = res[q];
   }
   double out[4];
-  block_sum_acc<4>(acc, red, out);
+  block_sum_short<4>(acc, red, out);
   if (threadIdx.x == 0) {
     const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
@@ -382,6 +418,7 @@ struct FinArgs {
   double dV, E_ion, Ne, scale, Q;  // Q = int psi_t^2 (mode 1); scale = N_e / Q
   double psid;                  // <psi_t, d> (mode 1)
   double mu_ref;                // reference subtracted from v_rest in g'
+  int merged;                   // NL carried by the psi field (E_NL scales, v_NL not in v_rest)
   int mode;
   double* res;
 };
@@ -399,10 +436,11 @@ static __device__ void finalize_eval(const FinArgs& f, double* red) {
   double s[12];
   block_sum<12>(acc, red, s);
   if (threadIdx.x == 0) {
-    const double E_H = s[0], E_loc = s[1], E_NL = s[2];
     const double scale = f.mode == 0 ? 1.0 : f.scale;
+    const double E_H = s[0], E_loc = s[1], E_NL = f.merged ? s[2] * scale : s[2];
     const double E_vW = s[3] * scale;
-    const double F_TF = s[4] * f.dV, E_xc = s[5] * f.dV, vn = s[6] * f.dV;
+    // int v_NL n = 2 a E_NL = E_NL for a = 1/2 (merged: v_NL is not in the epilogue's v_rest)
+    const double F_TF = s[4] * f.dV, E_xc = s[5] * f.dV, vn = s[6] * f.dV + (f.merged ? E_NL : 0.0);
     const double gd = s[7] * f.dV, gg = s[8] * f.dV, gpsi = s[9] * f.dV, ne = s[10] * f.dV;
     const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + f.E_ion;
     const double Ne = f.mode == 0 ? ne : f.Ne;
@@ -454,7 +492,7 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
   const int tot = R * n;
   const size_t off = row0 * n;
-  const float inh = 1.0f / (float)h;
+  const unsigned Mh = qmagic(h);
   // all spectrum rows of the block in flight at once (contiguous per field)
   for (int f = 0; f < sp.nact; ++f) {
     const cplx<T>* in = sp.s[sp.idx[f]] + row0 * nh;
@@ -472,7 +510,7 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     cplx<T>* in = stg + (size_t)f * Rfull * nh;
     // Z[k] = (X[k] + X*[h-k]) + i W^-k (X[k] - X*[h-k]),  k = 0..h-1
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
-      const int r = qdiv(q, inh), k = q - r * h;
+      const int r = qdiv(q, h, Mh), k = q - r * h;
       const cplx<T> xk = in[r * nh + k];
       const cplx<T> xc = cconj(in[r * nh + (h - k)]);
       const cplx<T> e = cadd(xk, xc);
@@ -484,7 +522,7 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     // real pairs land as one 8- or 16-byte store (R h complex <= R nh slots)
     cplx<T>* dst = in;
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
-      const int r = qdiv(q, inh), k = q - r * h;
+      const int r = qdiv(q, h, Mh), k = q - r * h;
       dst[r * h + k] = z[r * P + k];
     }
     realf[fid] = reinterpret_cast<T*>(in);
@@ -499,16 +537,20 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
   const T cy = a.cy;
   const T alpha = a.alpha, nmin = (T)kNmin;
   const T tstep = a.t, tscale = a.scale, muref = a.mu_ref;
-  Acc<T> acc[8];
+  AccShort<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
+  const T* __restrict__ gpsi = a.mode == 0 ? a.rho : a.psi;
+  const T* __restrict__ gd = a.d;
+  T* __restrict__ gout = a.out;
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    T psit, nval, dq = 0;
+    const T pv = gpsi[off + q];
+    const T dq = a.mode != 0 ? gd[off + q] : (T)0;
+    T psit, nval;
     if (a.mode == 0) {
-      nval = a.rho[off + q];
+      nval = pv;
       psit = sqrt(fmax(nval, (T)0));
     } else {
-      dq = a.d[off + q];
-      psit = a.psi[off + q] + tstep * dq;
+      psit = pv + tstep * dq;
       nval = tscale * psit * psit;
     }
     const T nf = fmax(nval, nmin);
@@ -527,20 +569,22 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     }
     if (has_n) vrest += fH[q];
     if (has_na) vrest += (T)2 * alpha * pow_t<T>(nf, alpha - (T)1) * fK[q];
-    const T lap = has_psi ? fL[q] : (T)0;   // -lap(psi)
+    // psi field: -lap(psi), or W = IFFT[(K + G^2/2) psi~] when merged
+    const T lw = has_psi ? fL[q] : (T)0;
+    const T extra = sp.merged ? lw : (T)0.5 * lw;     // psi v_NL + (-lap psi)/2 when merged
     acc[2].add(vrest * nval);
     acc[6].add(nval);
     // g' = psi (v_rest - mu_ref) + lap/2: near convergence mu_ref is close to
     // mu, so the projection g = 2 scale (g' - (mu - mu_ref) psi) cancels little
-    const T gp = psit * (vrest - muref) + (T)0.5 * lap;
+    const T gp = psit * (vrest - muref) + extra;
     if (a.mode == 0) {
       const T phi = fmax(psit, (T)kPhiMin);
-      const T v = vrest + lap / ((T)2 * phi);
-      if (a.out) a.out[off + q] = v;
+      const T v = vrest + extra / phi;
+      if (gout) gout[off + q] = v;
       // residual pieces with psi = sqrt(rho), scale 1: g' = psi v_rest + lap/2
       if (!isfinite(v)) acc[7].add((T)1);
     } else {
-      if (a.out) a.out[off + q] = gp;
+      if (gout) gout[off + q] = gp;
       acc[3].add(gp * dq);
       if (!isfinite(gp)) acc[7].add((T)1);
     }
@@ -548,7 +592,7 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     acc[5].add(gp * psit);
   }
   double out8[8];
-  block_sum_acc<8>(acc, red, out8);
+  block_sum_short<8>(acc, red, out8);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) a.partials[(size_t)blockIdx.x * 8 + q] = out8[q];
