@@ -210,6 +210,68 @@ __device__ __forceinline__ void block_sum_short(AccShort<T> (&a)[NQ], double* sc
   block_sum_acc<NQ>(b, scratch, out);
 }
 
+// Block sums through a shared-memory tree.  Reducing one value per lane with
+// warp shuffles redoes every addition on all 32 lanes (5 levels x 32 lanes
+// for 31 useful additions); with many per-thread sums that tail costs as much
+// as a streaming kernel's main loop.  Here each thread parks its nq values in
+// column q of a scratch array (row pitch blockDim + 1 against bank
+// conflicts), and the block adds pairs h apart, h = blockDim/2, ..., 1, every
+// thread taking a share of all columns' pairs.  Floats are carried as
+// (hi, lo) pairs added with TwoSum, so the tree adds no rounding error of
+// float order; the order is fixed, so results are deterministic.
+// blockDim must be a power of two; scratch holds nq * (blockDim + 1) values of
+// the scratch type (float2 / double).  dst[q] (global or shared) is written by
+// thread q < nq; the function begins and ends with a block barrier.
+template <typename T> struct TreeVal;
+template <> struct TreeVal<float> { using type = float2; };
+template <> struct TreeVal<double> { using type = double; };
+
+__device__ __forceinline__ float2 tree_add(float2 a, float2 b) {
+  const FF r = ff_add(FF{a.x, a.y}, FF{b.x, b.y});
+  return make_float2(r.hi, r.lo);
+}
+__device__ __forceinline__ double tree_add(double a, double b) { return a + b; }
+__device__ __forceinline__ double tree_get(float2 a) { return (double)a.x + (double)a.y; }
+__device__ __forceinline__ double tree_get(double a) { return a; }
+__device__ __forceinline__ float2 tree_put(const Acc<float>& a) {
+  const FF f = ff_from(a);
+  return make_float2(f.hi, f.lo);
+}
+__device__ __forceinline__ double tree_put(const Acc<double>& a) { return a.get(); }
+
+template <int NQMAX, typename T>
+__device__ __forceinline__ void block_sum_tree(const Acc<T>* a, int nq, double* dst,
+                                               typename TreeVal<T>::type* scr) {
+  const int nt = blockDim.x, pitch = nt + 1, t = threadIdx.x;
+  __syncthreads();                                   // scratch may alias data still being read
+#pragma unroll
+  for (int q = 0; q < NQMAX; ++q)
+    if (q < nq) scr[q * pitch + t] = tree_put(a[q]);
+  __syncthreads();
+  for (int h = nt >> 1, lg = __ffs(nt) - 2; h >= 1; h >>= 1, --lg) {
+    for (int w = t; w < nq * h; w += nt) {
+      const int q = w >> lg, i = w & (h - 1);
+      typename TreeVal<T>::type* c = scr + q * pitch;
+      c[i] = tree_add(c[i], c[i + h]);
+    }
+    __syncthreads();
+  }
+  if (t < nq) dst[t] = tree_get(scr[t * pitch]);
+  __syncthreads();
+}
+template <int NQ, typename T>
+__device__ __forceinline__ void block_sum_tree(const AccShort<T> (&a)[NQ], double* dst,
+                                               typename TreeVal<T>::type* scr) {
+  Acc<T> b[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) { b[q].s = a[q].s; if constexpr (sizeof(T) == 4) b[q].c = 0; }
+  block_sum_tree<NQ, T>(b, NQ, dst, scr);
+}
+template <typename T>
+__host__ __device__ constexpr size_t tree_scratch_bytes(int nq, int nt) {
+  return (size_t)nq * (nt + 1) * 8;   // float2 or double
+}
+
 // True in exactly one block: the last to arrive.  Every block must call it
 // (after its thread 0 has written the block's partial results); the last one
 // then reads all partials (use __ldcg) and resets the counter for the next
@@ -236,7 +298,16 @@ __device__ __forceinline__ void block_sum_columns(const double* partial, int row
   double v = 0;
   if (t < k * cols) {
     const int c = t % cols;
-    for (int r = t / cols; r < rows; r += k) v += __ldcg(partial + (size_t)r * cols + c);
+    // eight rows' loads in flight at a time, added in row order
+    int r = t / cols;
+    for (; r + 7 * k < rows; r += 8 * k) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = __ldcg(partial + (size_t)(r + u * k) * cols + c);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v += x[u];
+    }
+    for (; r < rows; r += k) v += __ldcg(partial + (size_t)r * cols + c);
   }
   colscr[t] = v;
   __syncthreads();
@@ -252,9 +323,9 @@ __device__ __forceinline__ void block_sum_columns(const double* partial, int row
 // warp reduces every value (float-float for float accumulators), lane 0 parks
 // it in shared memory, then thread q < nq adds the warp results in double and
 // writes dst[q] (deterministic).
+// wres: shared scratch of 32 * NQMAX doubles.
 template <int NQMAX, typename T>
-__device__ __forceinline__ void block_sum_many(const Acc<T>* a, int nq, double* dst) {
-  __shared__ double wres[32 * NQMAX];
+__device__ __forceinline__ void block_sum_many(const Acc<T>* a, int nq, double* dst, double* wres) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int q = 0; q < NQMAX; ++q) {

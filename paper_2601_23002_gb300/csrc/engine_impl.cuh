@@ -79,7 +79,7 @@ class Engine : public IEngine {
   // launch geometry
   int zR = 0, zP = 0, yJ = 0, xJ = 0;
   size_t smem_zf = 0, smem_zi = 0, smem_y = 0, smem_x = 0, smem_xp = 0;
-  int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_gram = 0, nsm = 152;
+  int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_stream = 0, nsm = 152;
   // device memory
   std::vector<void*> allocs;
   size_t nbytes = 0;
@@ -192,17 +192,20 @@ class Engine : public IEngine {
     if (tune.yJ >= 8 && tune.yJ <= 64 && pow2(tune.yJ)) yJ = tune.yJ;
     if (tune.xJ >= 8 && tune.xJ <= 64 && pow2(tune.xJ)) xJ = tune.xJ;
     smem_zf = align16((size_t)2 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
-    smem_zi = 3 * (size_t)zR * nh * sizeof(C) + 2 * (size_t)zR * zP * sizeof(C);
+    // (the G-space and epilogue passes reuse their tiles as reduction scratch)
+    smem_zi = std::max(3 * (size_t)zR * nh * sizeof(C) + 2 * (size_t)zR * zP * sizeof(C),
+                       tree_scratch_bytes<T>(8, kThreads));
     smem_y = 2 * (size_t)n * yJ * sizeof(C);
-    smem_x = 3 * (size_t)n * xJ * sizeof(C);
+    smem_x = std::max(3 * (size_t)n * xJ * sizeof(C), tree_scratch_bytes<T>(4, kThreads));
     smem_xp = 2 * (size_t)n * xJ * sizeof(C);
     grid_z = (int)(((size_t)n * n + zR - 1) / zR);
     grid_y1 = n * ((nh + yJ - 1) / yJ);
     grid_x = (int)(((size_t)n * nh + xJ - 1) / xJ);
     // streaming vector kernels: a multiple of the SM count (4 resident blocks
-    // per SM; the Gram pass holds ~126 registers per thread, so 2)
+    // per SM); the async-copy ring kernels hold 160 KB of shared memory, one
+    // block per SM
     grid_vec = (int)std::min<size_t>((size_t)4 * nsm, (N + kThreads - 1) / kThreads);
-    grid_gram = (int)std::min<size_t>((size_t)2 * nsm, (N + kThreads - 1) / kThreads);
+    grid_stream = (int)std::min<size_t>((size_t)nsm, (N / StreamCfg<T>::K + kStreamThreads - 1) / kStreamThreads);
   }
 
   size_t plan_bytes_estimate() {
@@ -268,6 +271,7 @@ class Engine : public IEngine {
     if ((rc = alloc(&res_d, 128))) return rc;
     if ((rc = alloc(&counters, 8))) return rc;
     OFDFT_CK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), st));
+    OFDFT_CK(cudaMemsetAsync(res_d, 0, 128 * sizeof(double), st));
     OFDFT_CK(cudaMallocHost(&res_h, 128 * sizeof(double)));
     if ((rc = alloc(&pos_d, (size_t)cs.Z.size() * 3))) return rc;
     if ((rc = alloc(&Z_d, cs.Z.size()))) return rc;
@@ -337,6 +341,17 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
     if ((rc = raise((const void*)k_xpass<T, -1>, smem_xp))) return rc;
+    const size_t sring = StreamCfg<T>::ring_bytes(3, 17);   // largest ring any streaming launch uses
+    if ((rc = raise((const void*)k_gram<T, 1, 3>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 2, 3>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 3, 3>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 4, 3>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 1, 2>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 2, 2>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 3, 2>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 4, 2>, sring))) return rc;
+    if ((rc = raise((const void*)k_lincomb<T>, sring))) return rc;
+    if ((rc = raise((const void*)k_accept<T>, sring))) return rc;
     return OFDFT_OK;
   }
 
@@ -500,25 +515,54 @@ class Engine : public IEngine {
     // every chunk's last block writes its columns to res_d[16 + c0 * nw ...]
     for (int c0 = 0; c0 < nv; c0 += kMaxV) {
       const int cn = std::min(kMaxV, nv - c0);
-      VecList<T> vl{}; vl.nv = cn;
-      for (int i = 0; i < cn; ++i) vl.v[i] = V[c0 + i];
-      VecList<T> wl{}; wl.nv = nw;
-      for (int j = 0; j < nw; ++j) wl.v[j] = W[j];
+      VecList<T> xl{}; xl.nv = cn + nw;
+      for (int i = 0; i < cn; ++i) xl.v[i] = V[c0 + i];
+      for (int j = 0; j < nw; ++j) xl.v[cn + j] = W[j];
       double* o = res_d + 16 + (size_t)c0 * nw;
+      const int S = cn + nw <= 17 ? 3 : 2;   // k_gram is built for 2 or 3 ring stages
+      const size_t sm = std::max(StreamCfg<T>::ring_bytes(S, cn + nw), tree_scratch_bytes<T>(cn * nw, kStreamThreads));
       prof.begin("k_gram", st, (double)(cn + nw) * N * sizeof(T));
-      switch (nw) {
-        case 1: k_gram<T, 1><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
-        case 2: k_gram<T, 2><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
-        case 3: k_gram<T, 3><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
-        default: k_gram<T, 4><<<grid_gram, kThreads, 0, st>>>(vl, wl, N, partials, counters + 1, o); break;
+      auto launch = [&](auto kern) { kern<<<grid_stream, kStreamThreads, sm, st>>>(xl, cn, N, partials, counters + 1, o); };
+      switch (nw * 8 + S) {
+        case 1 * 8 + 3: launch(k_gram<T, 1, 3>); break;
+        case 2 * 8 + 3: launch(k_gram<T, 2, 3>); break;
+        case 3 * 8 + 3: launch(k_gram<T, 3, 3>); break;
+        case 4 * 8 + 3: launch(k_gram<T, 4, 3>); break;
+        case 1 * 8 + 2: launch(k_gram<T, 1, 2>); break;
+        case 2 * 8 + 2: launch(k_gram<T, 2, 2>); break;
+        case 3 * 8 + 2: launch(k_gram<T, 3, 2>); break;
+        case 4 * 8 + 2: launch(k_gram<T, 4, 2>); break;
+        default: set_error("gram: no kernel for this list"); return OFDFT_ERR_INVALID;
       }
       prof.end(st);
       OFDFT_LAUNCH_CK();
     }
-    OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, (size_t)nv * nw * sizeof(double), cudaMemcpyDeviceToHost, st));
-    OFDFT_CK(cudaStreamSynchronize(st));
+    int rc;
+    if ((rc = read_results(st))) return rc;
     for (int i = 0; i < nv; ++i)
       for (int j = 0; j < nw; ++j) out[(size_t)i * nw + j] = res_h[16 + i * nw + j] * dV;
+    return OFDFT_OK;
+  }
+
+  // d = sum_i c_i V_i; returns <d,d>, <d,g>, <d,psi> (times dV)
+  int lincomb(const VecList<T>& terms, double* dd, double* dg, double* dpsi, cudaStream_t st) {
+    VecList<T> xl = terms;
+    const int nv = terms.nv;
+    xl.v[nv] = g; xl.v[nv + 1] = psi;
+    xl.nv = nv + 2;
+    OFDFT_RUN("k_lincomb", st, (double)(nv + 3) * N * sizeof(T),
+              k_lincomb<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(kMaxLin - 1), nv + 2), st>>>(
+                  xl, nv, d, N, partials, counters + 2, res_d + 16));
+    int rc;
+    if ((rc = read_results(st))) return rc;
+    *dd = res_h[16] * dV; *dg = res_h[17] * dV; *dpsi = res_h[18] * dV;
+    return OFDFT_OK;
+  }
+
+  // copy the reduction results res_d[16, 120) to the host
+  int read_results(cudaStream_t st) {
+    OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, (120 - 16) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    OFDFT_CK(cudaStreamSynchronize(st));
     return OFDFT_OK;
   }
 
@@ -710,10 +754,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     }
     double dd = 0, dg = 0, dpsi = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-      OFDFT_RUN("k_lincomb", st, (double)(vl.nv + 3) * N * sizeof(T), k_lincomb<T><<<grid_vec, kThreads, 0, st>>>(vl, d, g, psi, N, partials, counters + 2, res_d + 16));
-      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      OFDFT_CK(cudaStreamSynchronize(st));
-      dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
+      if ((rc = lincomb(vl, &dd, &dg, &dpsi, st))) return rc;
       if (dg < 0 || attempt == 1) break;
       // not a descent direction: drop the history and restart along -g
       ring.clear();
@@ -746,10 +787,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       ring.clear();
       VecList<T> v1{};
       v1.nv = 1; v1.v[0] = g; v1.c[0] = -1.0;
-      OFDFT_RUN("k_lincomb", st, 4.0 * N * sizeof(T), k_lincomb<T><<<grid_vec, kThreads, 0, st>>>(v1, d, g, psi, N, partials, counters + 2, res_d + 16));
-      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      OFDFT_CK(cudaStreamSynchronize(st));
-      dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
+      if ((rc = lincomb(v1, &dd, &dg, &dpsi, st))) return rc;
       if (dg < 0) {
         const double t1 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
         int lsev2 = 0;
@@ -764,7 +802,12 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     if (rc) return rc;
     // --- accept: s = t d, y = g_t - g, psi += t d, g = g_t  (the last trial is the accepted one)
     const int slot = ring.push();
-    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T), k_accept<T><<<grid_vec, kThreads, 0, st>>>(psi, d, (T)acc.t, gp, (T)(2.0 * lastScale), (T)(lastMu - mu_ref), g, Sh[slot], Yh[slot], N, partials, counters + 3, res_d + 120));
+    VecList<T> xa{};
+    xa.nv = 4; xa.v[0] = psi; xa.v[1] = d; xa.v[2] = gp; xa.v[3] = g;
+    OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T),
+              k_accept<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(4), 4), st>>>(
+                  xa, (T)acc.t, (T)(2.0 * lastScale), (T)(lastMu - mu_ref), psi, g, Sh[slot], Yh[slot], N,
+                  partials, counters + 3, res_d + 120));
     OFDFT_CK(cudaMemcpyAsync(res_h + 120, res_d + 120, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     new_slot = slot;
     mu_ref = lastMu;

@@ -310,7 +310,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftPlan1 pn,
                                                  const cplx<T>* __restrict__ tw_n, int n, int J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[4 * 32];
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* buf1 = buf0 + (size_t)n * J;
   cplx<T>* vbuf = buf1 + (size_t)n * J;
@@ -399,13 +398,10 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
     const int kx = q >> lgJ, j = q & (J - 1);
     if (j < jn) base[(size_t)kx * plane + j] = res[q];
   }
-  double out[4];
-  block_sum_short<4>(acc, red, out);
-  if (threadIdx.x == 0) {
-    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) g.partials[b * 4 + q] = out[q];
-  }
+  // the tile buffers are free now: reduce through them (dynamic smem is
+  // sized to hold the tree scratch)
+  const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  block_sum_tree<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
@@ -591,12 +587,8 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     acc[4].add(gp * gp);
     acc[5].add(gp * psit);
   }
-  double out8[8];
-  block_sum_short<8>(acc, red, out8);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) a.partials[(size_t)blockIdx.x * 8 + q] = out8[q];
-  }
+  block_sum_tree<8, T>(acc, a.partials + (size_t)blockIdx.x * 8,
+                       reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
   if (arrive_last(a.counter)) {
     finalize_eval(a.fin, red);
     if (threadIdx.x == 0) *a.counter = 0u;

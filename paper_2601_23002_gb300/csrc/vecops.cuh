@@ -5,9 +5,10 @@
 
 namespace ofdft {
 
-constexpr int kMaxV = 9;    // vectors per gram launch (longer lists are chunked)
+constexpr int kMaxV = 16;   // vectors per gram launch (longer lists are chunked)
 constexpr int kMaxW = 4;    // targets per gram launch
-constexpr int kMaxLin = 20; // terms of a linear combination (1 + 2 m, m <= 8)
+constexpr int kMaxLin = 20; // vectors of one streamed list: a combination's 1 + 2 m <= 17 terms and its
+                            // two dot targets, or kMaxV Gram vectors and kMaxW targets
 
 // 16-byte vector loads and stores of a real array (4 floats or 2 doubles).
 template <typename T> struct V16;
@@ -62,119 +63,192 @@ __global__ void k_project(T* __restrict__ g, const T* __restrict__ gp, const T* 
     g[i] = a * (gp[i] - m * psi[i]);
 }
 
-// All dot products <V_i, W_j>, i < nv <= kMaxV, j < NW.  Per block into
-// partial[block][i*NW + j]; the last block sums the columns into out[] in a
-// fixed order.  Products and per-thread sums in the vectors' precision
-// (compensated for float), block and grid sums in double.
-template <typename T, int NW>
-__global__ void __launch_bounds__(256) k_gram(VecList<T> V, VecList<T> W, size_t N, double* __restrict__ partial,
-                                              unsigned int* __restrict__ counter, double* __restrict__ out) {
+// The three streaming passes below read their vectors through a per-thread
+// ring of asynchronous copies (cp.async, 16 bytes per vector per thread) in
+// shared memory: S-1 groups' copies are in flight while the thread works on
+// the current one, without holding them in registers, so one 256-thread block
+// per SM keeps 70-140 KB in flight with ~100 registers per thread.  Each
+// thread reads back only what it copied itself, so the ring needs no block
+// barrier.  Ring layout: [S][nvec][blockDim] groups of 16 bytes.
+constexpr int kStreamThreads = 256;
+template <typename T> struct StreamCfg {
+  using V = typename V16<T>::type;                 // one 16-byte group (4 floats or 2 doubles)
+  static constexpr int K = V16<T>::K;
+  static constexpr size_t ring_bytes(int S, int nvec) { return (size_t)S * nvec * kStreamThreads * 16; }
+};
+// stages for a list of nvec vectors: as many as ~200 KB of ring allows
+__host__ __device__ constexpr int stream_stages(int nvec) { return nvec <= 4 ? 8 : nvec <= 17 ? 3 : 2; }
+
+template <typename T>
+__device__ __forceinline__ void lds16(const typename V16<T>::type* p, T (&o)[V16<T>::K]) {
+  const typename V16<T>::type v = *p;
+  memcpy(o, &v, sizeof(o));
+}
+
+// Groups p = blockIdx.x * blockDim.x + threadIdx.x + k * (gridDim.x *
+// blockDim.x) of the nvec <= kMaxLin vectors src.v[] (N elements each,
+// 16-byte aligned, N a multiple of the group size).  For every group the
+// thread calls body(mine, p), where mine[i * blockDim.x] is vector i's group
+// p in shared memory.
+template <typename T, int S, typename List, typename Body>
+__device__ __forceinline__ void cpa_stream(const List& src, int nvec, size_t N, unsigned char* smem, Body&& body) {
+  using V = typename V16<T>::type;
+  constexpr int K = V16<T>::K;
+  V* buf = reinterpret_cast<V*>(smem);
+  const size_t NG = N / K;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t p0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t iters = p0 < NG ? (NG - p0 + stride - 1) / stride : 0;
+  const size_t stage = (size_t)nvec * blockDim.x;
+  auto issue = [&](size_t k) {
+    V* dst = buf + (size_t)(k % S) * stage + threadIdx.x;
+    const size_t p = p0 + k * stride;
+#pragma unroll
+    for (int i = 0; i < kMaxLin; ++i)
+      if (i < nvec) cp_async<16>(dst + (size_t)i * blockDim.x, reinterpret_cast<const V*>(src.v[i]) + p, true);
+  };
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {
+    if ((size_t)k < iters) issue(k);
+    cp_async_commit();
+  }
+  for (size_t k = 0; k < iters; ++k) {
+    // the slot refilled here was last read by this thread in iteration k-1
+    if (k + S - 1 < iters) issue(k + S - 1);
+    cp_async_commit();
+    cp_async_wait<S - 1>();
+    body(buf + (size_t)(k % S) * stage + threadIdx.x, p0 + k * stride);
+  }
+  cp_async_wait<0>();
+}
+
+// All dot products <X_i, X_{nv+j}>, i < nv <= kMaxV, j < NW (X lists the nv
+// vectors, then the NW targets).  Per block into partial[block][i*NW + j]; the
+// last block sums the columns into out[] in a fixed order.  The products of a
+// group's K elements are summed in the vectors' precision and added to a
+// compensated per-thread sum (float); block and grid sums in double.
+template <typename T, int NW, int S>
+__global__ void __launch_bounds__(kStreamThreads, 1)
+k_gram(VecList<T> X, int nv, size_t N, double* __restrict__ partial, unsigned int* __restrict__ counter,
+       double* __restrict__ out) {
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[32];
+  using V = typename V16<T>::type;
   constexpr int K = V16<T>::K;
   Acc<T> acc[kMaxV][NW];
-  const int nv = V.nv;
-  const size_t NV = N / K;          // N is a multiple of 8 (even n)
-  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < NV; p += (size_t)gridDim.x * blockDim.x) {
-    // issue every 16-byte load of this group of K points before any use
-    T w[NW][K], a[kMaxV][K];
+  cpa_stream<T, S>(X, nv + NW, N, smem, [&](const V* mine, size_t) {
+    T w[NW][K];
 #pragma unroll
-    for (int j = 0; j < NW; ++j) ld16(W.v[j], p, w[j]);
-#pragma unroll
-    for (int i = 0; i < kMaxV; ++i) {
-      if (i < nv) ld16(V.v[i], p, a[i]);
-    }
+    for (int j = 0; j < NW; ++j) lds16<T>(mine + (size_t)(nv + j) * kStreamThreads, w[j]);
 #pragma unroll
     for (int i = 0; i < kMaxV; ++i) {
       if (i < nv) {
+        T a[K];
+        lds16<T>(mine + (size_t)i * kStreamThreads, a);
 #pragma unroll
-        for (int j = 0; j < NW; ++j)
+        for (int j = 0; j < NW; ++j) {
+          T t = a[0] * w[j][0];
 #pragma unroll
-          for (int k = 0; k < K; ++k) acc[i][j].add(a[i][k] * w[j][k]);
+          for (int k = 1; k < K; ++k) t = fma(a[k], w[j][k], t);
+          acc[i][j].add(t);
+        }
       }
     }
-  }
+  });
   const int cols = nv * NW;
-  block_sum_many<kMaxV * NW, T>(&acc[0][0], cols, partial + (size_t)blockIdx.x * cols);
+  // the ring is free: reuse it as reduction scratch (the host checks its size)
+  block_sum_tree<kMaxV * NW, T>(&acc[0][0], cols, partial + (size_t)blockIdx.x * cols,
+                                reinterpret_cast<typename TreeVal<T>::type*>(smem));
   if (arrive_last(counter)) {
     block_sum_columns(partial, gridDim.x, cols, out, red);
     if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
-// out = sum_i c_i V_i; the last block writes res[0..2] = <out,out>, <out,A>, <out,B>
+// out = sum_{i < nv} c_i X_i, with X_nv = A and X_{nv+1} = B; the last block
+// writes res[0..2] = <out,out>, <out,A>, <out,B>
 template <typename T>
-__global__ void __launch_bounds__(256) k_lincomb(VecList<T> V, T* __restrict__ out, const T* __restrict__ A,
-                                                 const T* __restrict__ B, size_t N, double* __restrict__ partial,
-                                                 unsigned int* __restrict__ counter, double* __restrict__ res) {
-  __shared__ double red[3 * 32];
+__global__ void __launch_bounds__(kStreamThreads, 1)
+k_lincomb(VecList<T> X, int nv, T* __restrict__ out, size_t N, double* __restrict__ partial,
+          unsigned int* __restrict__ counter, double* __restrict__ res) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[32];
+  using V = typename V16<T>::type;
+  constexpr int K = V16<T>::K;
   Acc<T> acc[3];
-  const int nv = V.nv;
-  T c[kMaxLin];
+  T c[kMaxLin - 2];
 #pragma unroll
-  for (int i = 0; i < kMaxLin; ++i) c[i] = i < nv ? (T)V.c[i] : (T)0;
-  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    T x[kMaxLin];
+  for (int i = 0; i < kMaxLin - 2; ++i) c[i] = i < nv ? (T)X.c[i] : (T)0;
+  cpa_stream<T, stream_stages(kMaxLin - 1)>(X, nv + 2, N, smem, [&](const V* mine, size_t p) {
+    T s[K];
 #pragma unroll
-    for (int i = 0; i < kMaxLin; ++i) x[i] = i < nv ? V.v[i][p] : (T)0;
-    const T av = A[p], bv = B[p];
-    T s = 0;
+    for (int k = 0; k < K; ++k) s[k] = 0;
 #pragma unroll
-    for (int i = 0; i < kMaxLin; ++i) s = fma(c[i], x[i], s);
-    out[p] = s;
-    acc[0].add(s * s);
-    acc[1].add(s * av);
-    acc[2].add(s * bv);
-  }
-  double r[3];
-  block_sum_acc<3>(acc, red, r);
-  if (threadIdx.x == 0) {
-    partial[(size_t)blockIdx.x * 3 + 0] = r[0];
-    partial[(size_t)blockIdx.x * 3 + 1] = r[1];
-    partial[(size_t)blockIdx.x * 3 + 2] = r[2];
-  }
+    for (int i = 0; i < kMaxLin - 2; ++i) {
+      if (i < nv) {
+        T x[K];
+        lds16<T>(mine + (size_t)i * kStreamThreads, x);
+#pragma unroll
+        for (int k = 0; k < K; ++k) s[k] = fma(c[i], x[k], s[k]);
+      }
+    }
+    T av[K], bv[K];
+    lds16<T>(mine + (size_t)nv * kStreamThreads, av);
+    lds16<T>(mine + (size_t)(nv + 1) * kStreamThreads, bv);
+    st16(out, p, s);
+    T t0 = s[0] * s[0], t1 = s[0] * av[0], t2 = s[0] * bv[0];
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      t0 = fma(s[k], s[k], t0); t1 = fma(s[k], av[k], t1); t2 = fma(s[k], bv[k], t2);
+    }
+    acc[0].add(t0); acc[1].add(t1); acc[2].add(t2);
+  });
+  block_sum_tree<3, T>(acc, 3, partial + (size_t)blockIdx.x * 3, reinterpret_cast<typename TreeVal<T>::type*>(smem));
   if (arrive_last(counter)) {
     block_sum_columns(partial, gridDim.x, 3, res, red);
     if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
-// Accept a line-search step tt along d:
+// Accept a line-search step tt along d (X = {psi, d, gp, g}):
 //   psi_t = psi + t d; g_t = 2 scale_t (gp - mu_t psi_t);
 //   s = psi_t - psi (= t d); y = g_t - g; psi <- psi_t; g <- g_t;
 // and, on the way, the dot products of the new pair with itself, the new
 // gradient and the new psi; the last block writes res[0..5] =
 //   <s,y>, <y,y>, <psi,psi>, <g,g>, <s,g>, <y,g>   (new psi, new g).
+// A thread rewrites psi and g only at the groups it has already copied in.
 template <typename T>
-__global__ void __launch_bounds__(256) k_accept(T* __restrict__ psi, const T* __restrict__ d, T tt,
-                                                const T* __restrict__ gp, T a, T m,
-                                                T* __restrict__ g, T* __restrict__ s, T* __restrict__ y, size_t N,
-                                                double* __restrict__ partial, unsigned int* __restrict__ counter,
-                                                double* __restrict__ res) {
-  __shared__ double red[6 * 32];
+__global__ void __launch_bounds__(kStreamThreads, 1)
+k_accept(VecList<T> X, T tt, T a, T m, T* __restrict__ psi, T* __restrict__ g, T* __restrict__ s,
+         T* __restrict__ y, size_t N, double* __restrict__ partial, unsigned int* __restrict__ counter,
+         double* __restrict__ res) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[32];
   // tt = step, a = 2 scale_t, m = mu_t - mu_ref (converted on the host)
+  using V = typename V16<T>::type;
   constexpr int K = V16<T>::K;
   Acc<T> acc[6];
-  const size_t NV = N / K;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < NV; i += (size_t)gridDim.x * blockDim.x) {
+  cpa_stream<T, stream_stages(4)>(X, 4, N, smem, [&](const V* mine, size_t p) {
     T p0[K], dd[K], gpi[K], g0[K], pt[K], gt[K], si[K], yi[K];
-    ld16(psi, i, p0); ld16(d, i, dd); ld16(gp, i, gpi); ld16(g, i, g0);
+    lds16<T>(mine, p0);
+    lds16<T>(mine + kStreamThreads, dd);
+    lds16<T>(mine + 2 * kStreamThreads, gpi);
+    lds16<T>(mine + 3 * kStreamThreads, g0);
+    T t[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       pt[k] = p0[k] + tt * dd[k];
       gt[k] = a * (gpi[k] - m * pt[k]);
       si[k] = pt[k] - p0[k];
       yi[k] = gt[k] - g0[k];
-      acc[0].add(si[k] * yi[k]); acc[1].add(yi[k] * yi[k]); acc[2].add(pt[k] * pt[k]);
-      acc[3].add(gt[k] * gt[k]); acc[4].add(si[k] * gt[k]); acc[5].add(yi[k] * gt[k]);
+      t[0] = fma(si[k], yi[k], t[0]); t[1] = fma(yi[k], yi[k], t[1]); t[2] = fma(pt[k], pt[k], t[2]);
+      t[3] = fma(gt[k], gt[k], t[3]); t[4] = fma(si[k], gt[k], t[4]); t[5] = fma(yi[k], gt[k], t[5]);
     }
-    st16(s, i, si); st16(y, i, yi); st16(psi, i, pt); st16(g, i, gt);
-  }
-  double r[6];
-  block_sum_acc<6>(acc, red, r);
-  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) partial[(size_t)blockIdx.x * 6 + q] = r[q];
-  }
+    for (int q = 0; q < 6; ++q) acc[q].add(t[q]);
+    st16(s, p, si); st16(y, p, yi); st16(psi, p, pt); st16(g, p, gt);
+  });
+  block_sum_tree<6, T>(acc, 6, partial + (size_t)blockIdx.x * 6, reinterpret_cast<typename TreeVal<T>::type*>(smem));
   if (arrive_last(counter)) {
     block_sum_columns(partial, gridDim.x, 6, res, red);
     if (threadIdx.x == 0) *counter = 0u;
