@@ -13,6 +13,7 @@
 #include "profiler.h"
 #include "fft.cuh"
 #include "passes.cuh"
+#include "plane.cuh"
 #include "setup.cuh"
 #include "vecops.cuh"
 
@@ -88,6 +89,13 @@ class Engine : public IEngine {
   T* Kt = nullptr;
   C* vloc = nullptr;
   C* Sg = nullptr;
+  // plane path (fused x-y-G-space pass; spectra in plane layout) when a kz
+  // plane fits in shared memory
+  bool plane_allowed = true;
+  bool planes = false;
+  size_t smem_pl = 0;
+  int* rev_d = nullptr;      // position -> frequency of the in-place transforms
+  C* vloc_pl = nullptr;      // V_loc in plane layout and position order
   C* spec[3] = {nullptr, nullptr, nullptr};
   T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
   T* Sh[kMaxMem] = {};
@@ -111,6 +119,8 @@ class Engine : public IEngine {
   explicit Engine(const CellSpec& c, int mmax) : cs(c), m_max(mmax) {
     auto env = [](const char* k) { const char* v = std::getenv(k); return v ? std::atoi(v) : 0; };
     tune.zR = env("OFDFT_ZR");
+    const char* pe = std::getenv("OFDFT_PLANE");
+    plane_allowed = !(pe && pe[0] == '0');
     tune.yJ = env("OFDFT_YJ");
     tune.xJ = env("OFDFT_XJ");
   }
@@ -164,6 +174,7 @@ class Engine : public IEngine {
     Spectra<T> s{};
     s.nact = 0;
     s.merged = merged() ? 1 : 0;
+    s.planes = planes ? 1 : 0;
     const bool on[3] = {use_n(), use_na() && !merged(), use_psi()};
     for (int f = 0; f < 3; ++f) {
       s.s[f] = on[f] ? spec[f] : nullptr;
@@ -201,6 +212,9 @@ class Engine : public IEngine {
     grid_z = (int)(((size_t)n * n + zR - 1) / zR);
     grid_y1 = n * ((nh + yJ - 1) / yJ);
     grid_x = (int)(((size_t)n * nh + xJ - 1) / xJ);
+    smem_pl = std::max(((size_t)n * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int),
+                       tree_scratch_bytes<T>(4, kPlaneThreads));
+    planes = plane_allowed && smem_pl <= (size_t)225 * 1024;
     // streaming vector kernels: a multiple of the SM count (4 resident blocks
     // per SM); the async-copy ring kernels hold 160 KB of shared memory, one
     // block per SM
@@ -212,6 +226,7 @@ class Engine : public IEngine {
     geometry();
     size_t b = 0;
     b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
+    if (planes) b += NH * sizeof(C);                         // vloc in plane order
     b += (4 + 2 * (size_t)m_max) * N * sizeof(T);            // psi d g gp + history
     b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
     b += (size_t)(n + h) * sizeof(C);
@@ -251,6 +266,26 @@ class Engine : public IEngine {
       if ((rc = alloc(&spec[f], NH))) return rc;
     if ((rc = alloc(&vloc, NH))) return rc;
     if ((rc = alloc(&Sg, NH))) return rc;
+    if (planes) {
+      // frequency at each position after the in-place forward stages:
+      // position p = sum_s k_s m_s (m_s = block length / R_s at stage s)
+      // holds frequency sum_s k_s R_1 ... R_(s-1)
+      std::vector<int> rev(n);
+      for (int p = 0; p < n; ++p) {
+        int rem = p, f = 0, mult = 1, Lsub = n;
+        for (int s2 = 0; s2 < pn.npass; ++s2) {
+          const int m = Lsub / pn.radix[s2];
+          f += (rem / m) * mult;
+          rem %= m;
+          mult *= pn.radix[s2];
+          Lsub = m;
+        }
+        rev[p] = f;
+      }
+      if ((rc = alloc(&rev_d, n))) return rc;
+      OFDFT_CK(cudaMemcpyAsync(rev_d, rev.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+      if ((rc = alloc(&vloc_pl, NH))) return rc;
+    }
     if ((rc = alloc(&psi, N))) return rc;
     if ((rc = alloc(&d, N))) return rc;
     if ((rc = alloc(&g, N))) return rc;
@@ -341,6 +376,7 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
     if ((rc = raise((const void*)k_xpass<T, -1>, smem_xp))) return rc;
+    if (planes && (rc = raise((const void*)k_plane<T>, smem_pl))) return rc;
     const size_t sring = StreamCfg<T>::ring_bytes(3, 17);   // largest ring any streaming launch uses
     if ((rc = raise((const void*)k_gram<T, 1, 3>, sring))) return rc;
     if ((rc = raise((const void*)k_gram<T, 2, 3>, sring))) return rc;
@@ -377,6 +413,7 @@ class Engine : public IEngine {
     OFDFT_RUN("k_fill", st, (double)N * sizeof(T), k_fill<T><<<grid_vec, kThreads, 0, st>>>(psi, (T)std::sqrt(nbar), N));
     const double Q = Ne / nbar;
     std::vector<int> rows{8, 16, 32}, cols{8, 16, 32};
+    if (planes) cols = {16};           // the plane pass has no column tiles
     const Tune saved = tune;
     double best = 1e300;
     int bt[3] = {0, 0, 0};
@@ -421,7 +458,8 @@ class Engine : public IEngine {
 
   // Sum columns of partials[rows][cols] into res_d[off ...] (fixed order).
   int sum_partials(int rows, int cols, int off, cudaStream_t st) {
-    OFDFT_RUN("k_sum_columns", st, (double)rows * cols * 8, k_sum_columns<<<(cols + 127) / 128, 128, 0, st>>>(partials, rows, cols, res_d + off));
+    if (cols > 256) { set_error("sum_partials: too many columns"); return OFDFT_ERR_INVALID; }
+    OFDFT_RUN("k_sum_columns", st, (double)rows * cols * 8, k_sum_columns<<<1, 256, 0, st>>>(partials, rows, cols, res_d + off));
     return OFDFT_OK;
   }
 
@@ -453,6 +491,8 @@ class Engine : public IEngine {
     double zz = 0;
     for (double z : cs.Z) zz += z * z;
     E_ion = res_h[0] + res_h[1] - eta / std::sqrt(kPi) * zz - kPi * Ne * Ne / (2.0 * Omega * eta * eta);
+    if (planes)
+      OFDFT_RUN("k_vloc_planes", st, 2.0 * NH * sizeof(C), k_vloc_planes<T><<<4 * nsm, 256, 0, st>>>(vloc, vloc_pl, rev_d, n));
     if (S_out) OFDFT_CK(cudaMemcpyAsync(S_out, Sg, NH * sizeof(C), cudaMemcpyDeviceToDevice, st));
     OFDFT_CK(cudaStreamSynchronize(st));
     ions_set = true;
@@ -465,20 +505,27 @@ class Engine : public IEngine {
            T* out, cudaStream_t st, bool sync, double mu_ref = 0.0) {
     Spectra<T> sp = spectra();
     ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha};
+    const double tp = 2.0 * kPi / L;
+    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? (planes ? vloc_pl : vloc) : nullptr, Kt, (T)(tp * tp), (T)Omega,
+                (T)(0.5 * Omega), (T)(1.0 / (double)N), (T)g2cut_loc, (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0,
+                partials};
+    int g_rows = 0;                       // rows of G-space partials [g_rows][4]
     if (sp.nact > 0) {
       OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
-      OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+      if (planes) {
+        OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_plane<T><<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
+        g_rows = nh * sp.nact;
+      } else {
+        OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+        OFDFT_RUN("k_xgspace", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_xgspace<T><<<dim3(grid_x, sp.nact), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
+        OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, 1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+        g_rows = grid_x * sp.nact;
+      }
     }
-    const double tp = 2.0 * kPi / L;
-    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? vloc : nullptr, Kt, (T)(tp * tp), (T)Omega, (T)(0.5 * Omega),
-                (T)(1.0 / (double)N), (T)g2cut_loc, (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0, partials};
-    if (sp.nact > 0) {
-      OFDFT_RUN("k_xgspace", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_xgspace<T><<<dim3(grid_x, sp.nact), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
-      OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, 1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
-    }
-    double* pe = partials + (size_t)grid_x * 3 * 4;      // after the x-pass partials [grid_x * nact][4]
+    // epilogue partials after room for 3 fields of G-space rows
+    double* pe = partials + (size_t)std::max(grid_x, nh) * 3 * 4;
     if (mode == 0) mu_ref = 0.0;
-    FinArgs fa{partials, grid_x * sp.nact, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, sp.merged, mode, res_d};
+    FinArgs fa{partials, g_rows, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, sp.merged, mode, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
     EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
                   counters + 0};

@@ -141,7 +141,7 @@ def main():
     ]
 
     def arr(name, tab, single, typ):
-        lines.append(f"static __device__ const {typ} {name}[{len(tab)}][{len(tab[0])}] = {{")
+        lines.append(f"static __device__ __align__(16) const {typ} {name}[{len(tab)}][{len(tab[0])}] = {{")
         for row in tab:
             lines.append("  {" + ", ".join(fmt(v, single) for v in row) + "},")
         lines.append("};")

@@ -34,6 +34,9 @@ template <typename T> struct Spectra {
   // so field 2 carries both terms: W = IFFT[(K + G^2/2) psi~] and
   // psi v_NL + (-lap psi)/2 = W (for psi >= 0); field 1 is not used
   int merged;
+  // layout of the half spectra: 0 = tiled [kx][ky][kz]; 1 = plane [kz][kx][ky]
+  // (entry (kz, x, y) at kz n^2 + x n + y, i.e. kz n^2 + real-space row)
+  int planes;
 };
 
 // ---------------------------------------------------------------------------
@@ -56,8 +59,15 @@ static __device__ __forceinline__ void fd_eta_p(double y, double& eta, double& p
     int i = (int)r;
     i = i < 0 ? 0 : (i >= FD64_NINT ? FD64_NINT - 1 : i);
     const double x = 2.0 * (r - (double)i) - 1.0;
-    const double* ce = fd64_eta[i];
-    const double* cp = fd64_p[i];
+    double ce[FD64_NC], cp[FD64_NC];
+    static_assert(FD64_NC % 2 == 0, "16-byte loads");
+    const double2* e2 = reinterpret_cast<const double2*>(fd64_eta[i]);
+    const double2* p2 = reinterpret_cast<const double2*>(fd64_p[i]);
+#pragma unroll
+    for (int k = 0; k < FD64_NC / 2; ++k) {
+      const double2 ev = __ldg(e2 + k), pv = __ldg(p2 + k);
+      ce[2 * k] = ev.x; ce[2 * k + 1] = ev.y; cp[2 * k] = pv.x; cp[2 * k + 1] = pv.y;
+    }
     double b1 = 0, b2 = 0, c1 = 0, c2 = 0;
 #pragma unroll
     for (int k = FD64_NC - 1; k >= 1; --k) {
@@ -85,8 +95,14 @@ static __device__ __forceinline__ void fd_eta_p(float y, float& eta, float& p) {
     int i = (int)r;
     i = i < 0 ? 0 : (i >= FD32_NINT ? FD32_NINT - 1 : i);
     const float x = 2.0f * (r - (float)i) - 1.0f;
-    const float* ce = fd32_eta[i];
-    const float* cp = fd32_p[i];
+    // each interval's 8 coefficients as two 16-byte loads per table
+    float ce[FD32_NC], cp[FD32_NC];
+    static_assert(FD32_NC == 8, "two float4 per interval");
+    const float4* e4 = reinterpret_cast<const float4*>(fd32_eta[i]);
+    const float4* p4 = reinterpret_cast<const float4*>(fd32_p[i]);
+    const float4 ea = __ldg(e4), eb = __ldg(e4 + 1), pa = __ldg(p4), pb = __ldg(p4 + 1);
+    ce[0] = ea.x; ce[1] = ea.y; ce[2] = ea.z; ce[3] = ea.w; ce[4] = eb.x; ce[5] = eb.y; ce[6] = eb.z; ce[7] = eb.w;
+    cp[0] = pa.x; cp[1] = pa.y; cp[2] = pa.z; cp[3] = pa.w; cp[4] = pb.x; cp[5] = pb.y; cp[6] = pb.z; cp[7] = pb.w;
     float b1 = 0, b2 = 0, c1 = 0, c2 = 0;
 #pragma unroll
     for (int k = FD32_NC - 1; k >= 1; --k) {
@@ -124,19 +140,19 @@ __device__ __forceinline__ void pz81(T n, T& exc, T& vxc) {
   vxc = vx + vc;
 }
 
-// FP32 plans: n^(1/3) from exp2/log2 and reciprocal multiplies (a few ulp,
-// inside float rounding of the terms they feed)
+// FP32 plans: fast reciprocals (__fdividef, a few ulp: inside the float
+// rounding of the terms they feed)
 template <>
 __device__ __forceinline__ void pz81<float>(float n, float& exc, float& vxc) {
-  const float cbn = exp2f(log2f(n) * (1.0f / 3.0f));
-  const float rs = 0.620350490899400017f * __frcp_rn(cbn);
+  const float cbn = cbrtf(n);
+  const float rs = __fdividef(0.620350490899400017f, cbn);
   const float ex = -0.738558766382022406f * cbn;
   const float vx = (4.0f / 3.0f) * ex;
   float ec, vc;
   if (rs >= 1.0f) {
     const float g = -0.1423f, b1 = 1.0529f, b2 = 0.3334f;
     const float sq = sqrtf(rs);
-    const float inv = __frcp_rn(1.0f + b1 * sq + b2 * rs);
+    const float inv = __fdividef(1.0f, 1.0f + b1 * sq + b2 * rs);
     ec = g * inv;
     vc = ec * (1.0f + (7.0f / 6.0f) * b1 * sq + (4.0f / 3.0f) * b2 * rs) * inv;
   } else {
@@ -196,7 +212,8 @@ __global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, Ff
   }
   __syncthreads();
   const T scale = a.scale, alpha = a.alpha, nmin = (T)kNmin;
-  const unsigned Mh = qmagic(h), Mnh = qmagic(nh);
+  const unsigned Mh = qmagic(h), Mnh = qmagic(nh), MR = qmagic(R);
+  const size_t nn = (size_t)n * n;
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
@@ -217,9 +234,13 @@ __global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, Ff
     __syncthreads();
     cplx<T>* Z = fft_smem<T, -1>(buf0, buf1, ph, 1, P, R, tw_h);
     // X[k] = (Z[k] + Z*[h-k])/2 - (i/2) W^k (Z[k] - Z*[h-k]),  k = 0..h
-    cplx<T>* out = sp.s[fid] + row0 * nh;
+    // (plane layout: consecutive threads take consecutive rows of one kz, so
+    // the block's stores form runs of R)
+    cplx<T>* out = sp.s[fid];
     for (int q = threadIdx.x; q < R * nh; q += blockDim.x) {
-      const int r = qdiv(q, nh, Mnh), k = q - r * nh;
+      int r, k;
+      if (sp.planes) { k = qdiv(q, R, MR); r = q - k * R; }
+      else { r = qdiv(q, nh, Mnh); k = q - r * nh; }
       const cplx<T> zk = Z[r * P + (k == h ? 0 : k)];
       const cplx<T> zc = cconj(Z[r * P + (k == 0 ? 0 : h - k)]);
       const cplx<T> e = cadd(zk, zc);
@@ -227,7 +248,8 @@ __global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, Ff
       const cplx<T> w = tw_n[k];
       const cplx<T> wo = cmul(w, o);
       // -(i/2) wo = (wo.y/2, -wo.x/2)
-      out[q] = mk<T>((T)0.5 * (e.x + wo.y), (T)0.5 * (e.y - wo.x));
+      const size_t at = sp.planes ? (size_t)k * nn + row0 + r : (row0 + r) * nh + k;
+      out[at] = mk<T>((T)0.5 * (e.x + wo.y), (T)0.5 * (e.y - wo.x));
     }
     __syncthreads();
   }
@@ -488,12 +510,22 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
   const int tot = R * n;
   const size_t off = row0 * n;
-  const unsigned Mh = qmagic(h);
-  // all spectrum rows of the block in flight at once (contiguous per field)
+  const unsigned Mh = qmagic(h), MR = qmagic(R);
+  const size_t nn = (size_t)n * n;
+  // all spectrum rows of the block in flight at once (tiled layout: contiguous
+  // per field; plane layout: runs of R rows per kz)
   for (int f = 0; f < sp.nact; ++f) {
-    const cplx<T>* in = sp.s[sp.idx[f]] + row0 * nh;
     cplx<T>* dst = stg + (size_t)f * Rfull * nh;
-    for (int q = threadIdx.x; q < R * nh; q += blockDim.x) cp_async_c(dst + q, in + q, true);
+    if (sp.planes) {
+      const cplx<T>* in = sp.s[sp.idx[f]] + row0;
+      for (int q = threadIdx.x; q < R * nh; q += blockDim.x) {
+        const int k = qdiv(q, R, MR), r = q - k * R;
+        cp_async_c(dst + r * nh + k, in + (size_t)k * nn + r, true);
+      }
+    } else {
+      const cplx<T>* in = sp.s[sp.idx[f]] + row0 * nh;
+      for (int q = threadIdx.x; q < R * nh; q += blockDim.x) cp_async_c(dst + q, in + q, true);
+    }
   }
   cp_async_commit();
   cp_async_wait<0>();

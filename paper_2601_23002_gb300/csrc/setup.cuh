@@ -297,12 +297,9 @@ __global__ void __launch_bounds__(256) k_sei_shells(const cplx<T>* __restrict__ 
   if (threadIdx.x == 0) { out[2 * s] = o[0]; out[2 * s + 1] = o[1]; }
 }
 
+// out[c] = sum_r partial[r * cols + c] in a fixed order; one block, cols <= blockDim.x
 static __global__ void k_sum_columns(const double* __restrict__ partial, int rows, int cols, double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  double s = 0;
-  for (int r = 0; r < rows; ++r) s += partial[(size_t)r * cols + c];
-  out[c] = s;
+  block_sum_columns(partial, rows, cols, out, nullptr);
 }
 
 }  // namespace ofdft

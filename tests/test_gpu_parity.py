@@ -101,6 +101,30 @@ def test_energy_potential_fp32(name, mk):
     assert np.max(np.abs(v - ref_v)) < 1e-4 * max(1.0, np.max(np.abs(ref_v)))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk", [CASES[2], CASES[4]])
+def test_plane_and_tiled_paths_match_oracle(precision, name, mk, monkeypatch):
+    """Grids whose kz planes fit in shared memory take the fused plane pass;
+    OFDFT_PLANE=0 forces the tiled y / x-G-space / y chain.  Both against the
+    oracle, and against each other (same arithmetic, other FFT factorisation
+    and summation order)."""
+    cell = mk()
+    rho = rand_density(cell, 5)
+    if precision == "fp32":
+        rho = rho.astype(np.float32).astype(np.float64)
+    ref_e, ref_v = Functional(cell).evaluate(rho)
+    e1, v1 = gpu_eval(cell, rho, precision=precision)
+    monkeypatch.setenv("OFDFT_PLANE", "0")
+    e2, v2 = gpu_eval(cell, rho, precision=precision)
+    tol_e, tol_v = (1e-9, 1e-8) if precision == "fp64" else (1e-5, 1e-4)
+    vmax = max(1.0, np.max(np.abs(ref_v)))
+    for e, v in ((e1, v1), (e2, v2)):
+        assert abs(e["F_total"] - ref_e["total"]) / cell.n_ion < tol_e
+        assert np.max(np.abs(v - ref_v)) < tol_v * vmax
+    assert abs(e1["F_total"] - e2["F_total"]) / cell.n_ion < tol_e
+    assert np.max(np.abs(v1 - v2)) < tol_v * vmax
+
+
 def test_structure_factor_matches_oracle():
     cell = random_cell(SEED_BASE + 31, 17, 1.0, 1.9, 1.0, 24)
     plan = og.Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc)
