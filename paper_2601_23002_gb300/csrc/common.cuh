@@ -239,23 +239,33 @@ __device__ __forceinline__ float2 tree_put(const Acc<float>& a) {
 }
 __device__ __forceinline__ double tree_put(const Acc<double>& a) { return a.get(); }
 
-template <int NQMAX, typename T>
-__device__ __forceinline__ void block_sum_tree(const Acc<T>* a, int nq, double* dst,
-                                               typename TreeVal<T>::type* scr) {
+// Tree over values already parked in scr (column q at scr + q * (blockDim + 1));
+// afterwards column q's sum sits in scr[q * (blockDim + 1)].
+template <typename V>
+__device__ __forceinline__ void block_tree_core(int nq, V* scr) {
   const int nt = blockDim.x, pitch = nt + 1, t = threadIdx.x;
-  __syncthreads();                                   // scratch may alias data still being read
-#pragma unroll
-  for (int q = 0; q < NQMAX; ++q)
-    if (q < nq) scr[q * pitch + t] = tree_put(a[q]);
   __syncthreads();
   for (int h = nt >> 1, lg = __ffs(nt) - 2; h >= 1; h >>= 1, --lg) {
     for (int w = t; w < nq * h; w += nt) {
       const int q = w >> lg, i = w & (h - 1);
-      typename TreeVal<T>::type* c = scr + q * pitch;
+      V* c = scr + q * pitch;
       c[i] = tree_add(c[i], c[i + h]);
     }
     __syncthreads();
   }
+}
+
+// Sums of per-thread accumulators a[0..nq) over the block; thread q < nq
+// writes column q's sum to dst[q] as a double.
+template <int NQMAX, typename T>
+__device__ __forceinline__ void block_sum_tree(const Acc<T>* a, int nq, double* dst,
+                                               typename TreeVal<T>::type* scr) {
+  const int pitch = blockDim.x + 1, t = threadIdx.x;
+  __syncthreads();                                   // scratch may alias data still being read
+#pragma unroll
+  for (int q = 0; q < NQMAX; ++q)
+    if (q < nq) scr[q * pitch + t] = tree_put(a[q]);
+  block_tree_core(nq, scr);
   if (t < nq) dst[t] = tree_get(scr[t * pitch]);
   __syncthreads();
 }
@@ -266,6 +276,25 @@ __device__ __forceinline__ void block_sum_tree(const AccShort<T> (&a)[NQ], doubl
 #pragma unroll
   for (int q = 0; q < NQ; ++q) { b[q].s = a[q].s; if constexpr (sizeof(T) == 4) b[q].c = 0; }
   block_sum_tree<NQ, T>(b, NQ, dst, scr);
+}
+// As above, but the sums stay in tree form (float-float pairs for float,
+// doubles for double): dst[q] = column q's sum.  Partial sums that a later
+// pass adds up stay on the FP32 pipe this way.
+template <int NQ, typename T>
+__device__ __forceinline__ void block_sum_tree_raw(const AccShort<T> (&a)[NQ], typename TreeVal<T>::type* dst,
+                                                   typename TreeVal<T>::type* scr) {
+  const int pitch = blockDim.x + 1, t = threadIdx.x;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    Acc<T> b;
+    b.s = a[q].s;
+    if constexpr (sizeof(T) == 4) b.c = 0;
+    scr[q * pitch + t] = tree_put(b);
+  }
+  block_tree_core(NQ, scr);
+  if (t < NQ) dst[t] = scr[t * pitch];
+  __syncthreads();
 }
 template <typename T>
 __host__ __device__ constexpr size_t tree_scratch_bytes(int nq, int nt) {

@@ -185,6 +185,14 @@ class Engine : public IEngine {
 
   static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+  // epilogue pass: staging of the active spectra, two FFT buffers, the block's
+  // rho or psi and d rows
+  size_t zinv_bytes(int r) const {
+    const int nact = spectra().nact;
+    const int P = (n / 2 + 1) | 1;
+    return (size_t)nact * r * (n / 2 + 1) * sizeof(C) + 2 * (size_t)r * P * sizeof(C) + 2 * (size_t)r * n * sizeof(T);
+  }
+
   void geometry() {
     n = cs.n; h = n / 2; nh = h + 1;
     N = (size_t)n * n * n;
@@ -204,8 +212,7 @@ class Engine : public IEngine {
     if (tune.xJ >= 8 && tune.xJ <= 64 && pow2(tune.xJ)) xJ = tune.xJ;
     smem_zf = align16((size_t)2 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
     // (the G-space and epilogue passes reuse their tiles as reduction scratch)
-    smem_zi = std::max(3 * (size_t)zR * nh * sizeof(C) + 2 * (size_t)zR * zP * sizeof(C),
-                       tree_scratch_bytes<T>(8, kThreads));
+    smem_zi = std::max(zinv_bytes(zR), tree_scratch_bytes<T>(12, kThreads));   // finalize: 12 columns
     smem_y = 2 * (size_t)n * yJ * sizeof(C);
     smem_x = std::max(3 * (size_t)n * xJ * sizeof(C), tree_scratch_bytes<T>(4, kThreads));
     smem_xp = 2 * (size_t)n * xJ * sizeof(C);
@@ -348,7 +355,7 @@ class Engine : public IEngine {
     const size_t lim = 227 * 1024;
     const int P = nh | 1;
     const size_t zf = align16((size_t)2 * r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
-    const size_t zi = 3 * (size_t)r * nh * sizeof(C) + 2 * (size_t)r * P * sizeof(C);
+    const size_t zi = zinv_bytes(r);
     const size_t yx = 3 * (size_t)n * j * sizeof(C);
     return r >= 8 && j >= 8 && (j & (j - 1)) == 0 && zf <= lim && zi <= lim && yx <= lim && j <= 64 && r <= 64;
   }
@@ -506,9 +513,11 @@ class Engine : public IEngine {
     Spectra<T> sp = spectra();
     ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha};
     const double tp = 2.0 * kPi / L;
+    using TV = typename TreeVal<T>::type;          // 8 bytes, like the double slots of partials
+    TV* pt = reinterpret_cast<TV*>(partials);
     GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? (planes ? vloc_pl : vloc) : nullptr, Kt, (T)(tp * tp), (T)Omega,
                 (T)(0.5 * Omega), (T)(1.0 / (double)N), (T)g2cut_loc, (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0,
-                partials};
+                pt};
     int g_rows = 0;                       // rows of G-space partials [g_rows][4]
     if (sp.nact > 0) {
       OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
@@ -523,18 +532,46 @@ class Engine : public IEngine {
       }
     }
     // epilogue partials after room for 3 fields of G-space rows
-    double* pe = partials + (size_t)std::max(grid_x, nh) * 3 * 4;
+    TV* pe = pt + (size_t)std::max(grid_x, nh) * 3 * 4;
     if (mode == 0) mu_ref = 0.0;
-    FinArgs fa{partials, g_rows, pe, grid_z, dV, E_ion, Ne, scale, Q, psid, mu_ref, sp.merged, mode, res_d};
+    FinArgs<T> fa{pt, g_rows, pe, grid_z, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
     EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
                   counters + 0};
     OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
-      OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 14 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaStreamSynchronize(st));
+      finish_eval(mode, scale, Q, psid, mu_ref, sp.merged != 0);
     }
     return OFDFT_OK;
+  }
+
+  // From the 12 raw sums in res_h[0..11] (see finalize_eval) to
+  // res_h: 0 F_TF 1 E_vW 2 E_NL 3 E_H 4 E_loc 5 E_xc 6 E_ion 7 F_total 8 N_e
+  // 9 mu 10 residual 11 slope <g, d> 12 int v_rest n 13 nonfinite count.
+  void finish_eval(int mode, double scale_t, double Q_t, double psid, double mu_ref, bool merg) {
+    double s[12];
+    std::memcpy(s, res_h, sizeof(s));
+    const double scale = mode == 0 ? 1.0 : scale_t;
+    const double E_H = s[0], E_loc = s[1], E_NL = merg ? s[2] * scale : s[2];
+    const double E_vW = s[3] * scale;
+    // int v_NL n = 2 a E_NL = E_NL for a = 1/2 (merged: v_NL is not in the epilogue's v_rest)
+    const double F_TF = s[4] * dV, E_xc = s[5] * dV, vn = s[6] * dV + (merg ? E_NL : 0.0);
+    const double gd = s[7] * dV, gg = s[8] * dV, gpsi = s[9] * dV, ne = s[10] * dV;
+    const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + E_ion;
+    const double Nel = mode == 0 ? ne : Ne;
+    const double mu = (vn + E_vW) / Nel;
+    // residual^2 = (1/Q) int (g' - (mu - mu_ref) psi)^2, Q = int psi^2 (= N_e for mode 0)
+    const double Q = mode == 0 ? ne : Q_t;
+    const double dm = mu - mu_ref;
+    const double r2 = (gg - 2.0 * dm * gpsi + dm * dm * Q) / Q;
+    double* r = res_h;
+    r[0] = F_TF; r[1] = E_vW; r[2] = E_NL; r[3] = E_H; r[4] = E_loc; r[5] = E_xc; r[6] = E_ion;
+    r[7] = tot; r[8] = ne; r[9] = mu; r[10] = std::sqrt(std::max(r2, 0.0));
+    // slope dE/dt = <g, d> with g = 2 scale (g' - (mu - mu_ref) psi_t)
+    r[11] = 2.0 * scale * (gd - dm * psid);
+    r[12] = vn; r[13] = s[11];
   }
 
   int energy_potential(const void* rho, void* v_out, ofdft_energies* e, void* stream_) override {

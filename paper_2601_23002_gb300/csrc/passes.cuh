@@ -181,7 +181,7 @@ template <typename T> struct ProArgs {
 
 // smem: psit[R][n] (T) | dbuf[R][n] (T) | buf0[R][P] | buf1[R][P] (complex)
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPlan1 ph,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPlan1 ph,
                                               const cplx<T>* __restrict__ tw_h,
                                               const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -323,7 +323,9 @@ template <typename T> struct GArgs {
   T Om, halfOm, invN;    // Omega, Omega/2, 1/N
   T g2cut_loc;           // V_loc negligible beyond this |G|^2
   int hartree;           // 1: add 4 pi n~/G^2 to the n field
-  double* partials;      // [gridDim.y * gridDim.x][4]: E_H, E_loc, E_NL, E_vW(raw)
+  // [gridDim.y * gridDim.x][4]: E_H, E_loc, E_NL, E_vW(raw), as float-float
+  // pairs (FP32 plans) or doubles
+  typename TreeVal<T>::type* partials;
 };
 
 // One block per (tile, field): blockIdx.y indexes the active fields.
@@ -423,57 +425,67 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
   // the tile buffers are free now: reduce through them (dynamic smem is
   // sized to hold the tree scratch)
   const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-  block_sum_tree<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
+  block_sum_tree_raw<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
-// Final reduction of one evaluation, by one block (fixed order: deterministic).
-// res[]: 0 F_TF 1 E_vW 2 E_NL 3 E_H 4 E_loc 5 E_xc 6 E_ion 7 F_total 8 N_e 9 mu
-//        10 residual 11 slope <g, d> 12 int v_rest n 13 nonfinite count
-struct FinArgs {
-  const double* pg; int ng;     // G-space partials [ng][4]
-  const double* pe; int ne;     // epilogue partials [ne][8]
-  double dV, E_ion, Ne, scale, Q;  // Q = int psi_t^2 (mode 1); scale = N_e / Q
-  double psid;                  // <psi_t, d> (mode 1)
-  double mu_ref;                // reference subtracted from v_rest in g'
-  int merged;                   // NL carried by the psi field (E_NL scales, v_NL not in v_rest)
-  int mode;
-  double* res;
+// Final reduction of one evaluation, by the last block (fixed order:
+// deterministic).  It only adds: out[0..3] = sums of the G-space columns
+// (E_H, E_loc, E_NL, E_vW raw), out[4..11] = sums of the epilogue columns
+// (F_TF, E_xc, int v_rest n, int g' d, int g'^2, int g' psi_t, int n,
+// nonfinite count), all before the dV and scale factors.  The host, which
+// reads them anyway, forms the energies, mu, the residual and the slope:
+// GB300 issues FP64 at 1/64 of the FP32 rate, so even one thread's divisions
+// and square roots here would be a serial tail of several microseconds.  For
+// the same reason the partials are float-float pairs in FP32 plans and are
+// added on the FP32 pipe.
+template <typename T> struct FinArgs {
+  using V = typename TreeVal<T>::type;
+  const V* pg; int ng;          // G-space partials [ng][4]
+  const V* pe; int ne;          // epilogue partials [ne][8]
+  double* out;                  // [12]
 };
 
-static __device__ void finalize_eval(const FinArgs& f, double* red) {
-  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < f.ng; b += blockDim.x) {
+template <typename T>
+static __device__ void finalize_eval(const FinArgs<T>& f, typename TreeVal<T>::type* scr) {
+  using V = typename TreeVal<T>::type;
+  V acc[12];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += __ldcg(f.pg + (size_t)b * 4 + q);
-  }
-  for (int b = threadIdx.x; b < f.ne; b += blockDim.x) {
+  for (int q = 0; q < 12; ++q) acc[q] = V{};
+  const int nt = blockDim.x;
+  // a thread's next rows' loads are in flight together, added in row order
+  for (int b0 = threadIdx.x; b0 < f.ng; b0 += 4 * nt) {
+    V x[4][4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[4 + q] += __ldcg(f.pe + (size_t)b * 8 + q);
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + u * nt;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[u][q] = b < f.ng ? __ldcg(f.pg + (size_t)b * 4 + q) : V{};
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = tree_add(acc[q], x[u][q]);
   }
-  double s[12];
-  block_sum<12>(acc, red, s);
-  if (threadIdx.x == 0) {
-    const double scale = f.mode == 0 ? 1.0 : f.scale;
-    const double E_H = s[0], E_loc = s[1], E_NL = f.merged ? s[2] * scale : s[2];
-    const double E_vW = s[3] * scale;
-    // int v_NL n = 2 a E_NL = E_NL for a = 1/2 (merged: v_NL is not in the epilogue's v_rest)
-    const double F_TF = s[4] * f.dV, E_xc = s[5] * f.dV, vn = s[6] * f.dV + (f.merged ? E_NL : 0.0);
-    const double gd = s[7] * f.dV, gg = s[8] * f.dV, gpsi = s[9] * f.dV, ne = s[10] * f.dV;
-    const double tot = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + f.E_ion;
-    const double Ne = f.mode == 0 ? ne : f.Ne;
-    const double mu = (vn + E_vW) / Ne;
-    // residual^2 = (1/Q) int (g' - (mu - mu_ref) psi)^2, Q = int psi^2 (= N_e for mode 0)
-    const double Q = f.mode == 0 ? ne : f.Q;
-    const double dm = mu - f.mu_ref;
-    const double r2 = (gg - 2.0 * dm * gpsi + dm * dm * Q) / Q;
-    double* r = f.res;
-    r[0] = F_TF; r[1] = E_vW; r[2] = E_NL; r[3] = E_H; r[4] = E_loc; r[5] = E_xc; r[6] = f.E_ion;
-    r[7] = tot; r[8] = ne; r[9] = mu; r[10] = sqrt(fmax(r2, 0.0));
-    // slope dE/dt = <g, d> with g = 2 scale (g' - (mu - mu_ref) psi_t)
-    r[11] = 2.0 * scale * (gd - dm * f.psid);
-    r[12] = vn; r[13] = s[11];
+  for (int b0 = threadIdx.x; b0 < f.ne; b0 += 2 * nt) {
+    V x[2][8];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int b = b0 + u * nt;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[u][q] = b < f.ne ? __ldcg(f.pe + (size_t)b * 8 + q) : V{};
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[4 + q] = tree_add(acc[4 + q], x[u][q]);
   }
+  const int pitch = nt + 1;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 12; ++q) scr[q * pitch + threadIdx.x] = acc[q];
+  block_tree_core(12, scr);
+  if (threadIdx.x < 12) f.out[threadIdx.x] = tree_get(scr[threadIdx.x * pitch]);
 }
 
 // ---------------------------------------------------------------------------
@@ -488,23 +500,25 @@ template <typename T> struct EpiArgs {
   T mu_ref;              // g' is formed with v_rest - mu_ref (mode 1), see FinArgs
   int terms;             // OFDFT_TERM_* mask
   T* out;                // v (mode 0) or g' = psi_t v_rest + lap/2 (mode 1); may be null
-  double* partials;      // [gridDim.x][8]
-  FinArgs fin;           // final reduction, done by the last block to finish
+  typename TreeVal<T>::type* partials;   // [gridDim.x][8], tree form (see GArgs)
+  FinArgs<T> fin;        // final reduction, done by the last block to finish
   unsigned int* counter;
 };
 
-// smem: stg[3][R][nh] (complex; field f's real rows overwrite its own staging
-// once it has been pre-processed) | buf0[R][P] | buf1[R][P]
+// smem: stg[nact][R][nh] (complex; field f's real rows overwrite its own
+// staging once it has been pre-processed) | buf0[R][P] | buf1[R][P] |
+// pin[2][R][n] (the block's rho, or psi and d, copied in with the spectra so
+// that the pointwise loop does not wait on memory)
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, FftPlan1 ph,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a, FftPlan1 ph,
                                                      const cplx<T>* __restrict__ tw_h,
                                                      const cplx<T>* __restrict__ tw_n, int n, int R, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[12 * 32];
   const int h = n / 2, nh = h + 1;
   cplx<T>* stg = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* buf0 = stg + (size_t)3 * R * nh;
+  cplx<T>* buf0 = stg + (size_t)sp.nact * R * nh;
   cplx<T>* buf1 = buf0 + (size_t)R * P;
+  T* pin = reinterpret_cast<T*>(buf1 + (size_t)R * P);
   const size_t row0 = (size_t)blockIdx.x * R;
   const int Rfull = R;
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
@@ -525,6 +539,17 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     } else {
       const cplx<T>* in = sp.s[sp.idx[f]] + row0 * nh;
       for (int q = threadIdx.x; q < R * nh; q += blockDim.x) cp_async_c(dst + q, in + q, true);
+    }
+  }
+  {
+    // rows of rho (mode 0) or psi and d (mode 1) in 8-byte pieces (n is even,
+    // so every row starts on an 8-byte boundary)
+    constexpr int E = 8 / sizeof(T);
+    const int pieces = tot / E;
+    const T* src0 = a.mode == 0 ? a.rho : a.psi;
+    for (int q = threadIdx.x; q < pieces; q += blockDim.x) {
+      cp_async<8>(pin + q * E, src0 + off + q * E, true);
+      if (a.mode != 0) cp_async<8>(pin + (size_t)Rfull * n + q * E, a.d + off + q * E, true);
     }
   }
   cp_async_commit();
@@ -567,12 +592,11 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
   const T tstep = a.t, tscale = a.scale, muref = a.mu_ref;
   AccShort<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
-  const T* __restrict__ gpsi = a.mode == 0 ? a.rho : a.psi;
-  const T* __restrict__ gd = a.d;
+  const T* pd = pin + (size_t)Rfull * n;
   T* __restrict__ gout = a.out;
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    const T pv = gpsi[off + q];
-    const T dq = a.mode != 0 ? gd[off + q] : (T)0;
+    const T pv = pin[q];
+    const T dq = a.mode != 0 ? pd[q] : (T)0;
     T psit, nval;
     if (a.mode == 0) {
       nval = pv;
@@ -619,10 +643,10 @@ __global__ void __launch_bounds__(256, 4) k_zinv_epi(Spectra<T> sp, EpiArgs<T> a
     acc[4].add(gp * gp);
     acc[5].add(gp * psit);
   }
-  block_sum_tree<8, T>(acc, a.partials + (size_t)blockIdx.x * 8,
-                       reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
+  typename TreeVal<T>::type* scr = reinterpret_cast<typename TreeVal<T>::type*>(smem_raw);
+  block_sum_tree_raw<8, T>(acc, a.partials + (size_t)blockIdx.x * 8, scr);
   if (arrive_last(a.counter)) {
-    finalize_eval(a.fin, red);
+    finalize_eval<T>(a.fin, scr);
     if (threadIdx.x == 0) *a.counter = 0u;
   }
 }

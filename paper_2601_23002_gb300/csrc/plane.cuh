@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
     gpl[q] = a[r * pitch + c];
   }
   const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
-  block_sum_tree<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
+  block_sum_tree_raw<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
 }
 
 // One-time reorder of V_loc from the tiled layout [kx][ky][kz] into plane
