@@ -188,15 +188,24 @@ def run_ours(args, rank, world, local):
     plan, rho, pos = make("fp32")
     for _ in range(args.warmup):
         step(plan, rho, pos)
-    plan.profile_enable(True)
+    # the timed region: launches are counted, but no event pair is recorded
+    # around each launch (those pairs serialise the stream and cost ~15%)
+    plan.profile_enable(False)
     barrier()
     with ClockSampler(local) as clk:
         total_ms, evals, iters, last = timed(plan, rho, pos, args.steps)
     barrier()
-    prof = plan.profile_read()
+    counts = plan.profile_read()
     total_ms_max = max_over_ranks(total_ms)
+    # per-kernel device times for the roofline: the same steps again, with a
+    # CUDA-event pair around every launch on the library's stream
+    plan.profile_enable(True)
+    barrier()
+    prof_ms, _, _, _ = timed(plan, rho, pos, args.steps)
+    barrier()
+    prof = plan.profile_read()
     res["fp32"] = dict(total_ms=total_ms, total_ms_max=total_ms_max, evals=evals, iters=iters, last=last,
-                       prof=prof, clocks=clk.summary())
+                       prof=prof, counts=counts, profiled_ms=prof_ms, clocks=clk.summary())
 
     # end to end through the public API with host buffers: positions copied in,
     # converged density and energies copied out, every step
@@ -416,7 +425,7 @@ def main():
     evals_per_s = world * r32["evals"] / secs
     b_eval = 14 * N * 4
     prof = r32["prof"]
-    launches = sum(v[0] for v in prof.values())
+    launches = sum(v[0] for v in r32["counts"].values())
     line = {
         "metric": METRIC, "value": value, "unit": "snapshots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r32["total_ms_max"] / args.steps, "higher_is_better": True,
@@ -433,6 +442,8 @@ def main():
                 "h2d_bytes_per_step": res["e2e"]["h2d"], "d2h_bytes_per_step": res["e2e"]["d2h"]},
         "gpu_launches": launches,
         "roofline": roofline(prof),
+        "profiled_ms_per_step": r32["profiled_ms"] / args.steps,
+        "profiled_note": "kernels and roofline come from a second pass over the same steps with an event pair around every launch; value and ms_per_step from the pass without them",
         "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "GBps": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
     }
