@@ -511,7 +511,9 @@ class Engine : public IEngine {
   int eval(int mode, const T* rho, const T* ps, const T* dd, double t, double scale, double Q, double psid,
            T* out, cudaStream_t st, bool sync, double mu_ref = 0.0) {
     Spectra<T> sp = spectra();
-    ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha};
+    // psi of the uniform density: sqrt(nbar) for a given rho, sqrt(nbar / scale) for psi + t d
+    const double psi_bar = std::sqrt(nbar / (mode == 0 ? 1.0 : scale));
+    ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)psi_bar};
     const double tp = 2.0 * kPi / L;
     using TV = typename TreeVal<T>::type;          // 8 bytes, like the double slots of partials
     TV* pt = reinterpret_cast<TV*>(partials);
