@@ -98,6 +98,8 @@ class Engine : public IEngine {
   C* vloc_pl = nullptr;      // V_loc in plane layout and position order
   C* spec[3] = {nullptr, nullptr, nullptr};
   T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
+  // preconditioned two-loop recursion: q, P q and the table p(m^2)
+  T *qv = nullptr, *rv = nullptr, *precT = nullptr;
   T* Sh[kMaxMem] = {};
   T* Yh[kMaxMem] = {};
   double* partials = nullptr;
@@ -234,7 +236,7 @@ class Engine : public IEngine {
     size_t b = 0;
     b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
     if (planes) b += NH * sizeof(C);                         // vloc in plane order
-    b += (4 + 2 * (size_t)m_max) * N * sizeof(T);            // psi d g gp + history
+    b += (6 + 2 * (size_t)m_max) * N * sizeof(T);            // psi d g gp q Pq + history
     b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
     b += (size_t)(n + h) * sizeof(C);
     return b;
@@ -297,6 +299,8 @@ class Engine : public IEngine {
     if ((rc = alloc(&d, N))) return rc;
     if ((rc = alloc(&g, N))) return rc;
     if ((rc = alloc(&gp, N))) return rc;
+    if ((rc = alloc(&qv, N))) return rc;
+    if ((rc = alloc(&rv, N))) return rc;
     for (int i = 0; i < m_max; ++i) {
       if ((rc = alloc(&Sh[i], N))) return rc;
       if ((rc = alloc(&Yh[i], N))) return rc;
@@ -334,6 +338,19 @@ class Engine : public IEngine {
       OFDFT_CK(cudaMemsetAsync(Kd, 0, nm2 * sizeof(double), st));
     }
     OFDFT_RUN("k_convert_table", st, (double)nm2 * (8 + sizeof(T)), k_convert_table<T><<<(nm2 + 255) / 256, 256, 0, st>>>(Kd, Kt, nm2));
+    {
+      // kinetic preconditioner of the minimiser: p(G) = c / (c + G^2/2) with
+      // c = k_F^2/2 of the mean density (the scale below which the Thomas-Fermi
+      // response, not the vW kinetic term, sets the curvature)
+      const double kF = std::cbrt(3.0 * kPi * kPi * nbar);
+      const double c = 0.5 * kF * kF;
+      const double tp2d = (2.0 * kPi / L) * (2.0 * kPi / L);
+      std::vector<T> ph_(nm2);
+      for (int m2 = 0; m2 < nm2; ++m2) ph_[m2] = (T)(c / (c + 0.5 * tp2d * m2));
+      if ((rc = alloc(&precT, nm2))) return rc;
+      OFDFT_CK(cudaMemcpyAsync(precT, ph_.data(), nm2 * sizeof(T), cudaMemcpyHostToDevice, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+    }
     g2cut_loc = 156.0 / (cs.rc * cs.rc);
     {
       const double tp2 = (2.0 * kPi / L) * (2.0 * kPi / L);
@@ -549,6 +566,34 @@ class Engine : public IEngine {
     return OFDFT_OK;
   }
 
+  // out = P in = IFFT[p(G) FFT(in)/N]: the psi-field transform chain on a
+  // plain vector with the G-space factor p(m^2) (GArgs::prec, EpiArgs mode 3)
+  int precondition(const T* in, T* out, cudaStream_t st) {
+    Spectra<T> sp{};
+    sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = planes ? 1 : 0;
+    ProArgs<T> pa{1, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)0};
+    const double tp = 2.0 * kPi / L;
+    using TV = typename TreeVal<T>::type;
+    TV* pt = reinterpret_cast<TV*>(partials);
+    GArgs<T> ga{nullptr, Kt, (T)(tp * tp), (T)Omega, (T)(0.5 * Omega), (T)(1.0 / (double)N), (T)g2cut_loc, 0, pt,
+                precT};
+    const double fb = 2.0 * NH * sizeof(C);
+    OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+    if (planes) {
+      OFDFT_RUN("k_plane", st, fb, k_plane<T><<<dim3(nh, 1), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
+    } else {
+      OFDFT_RUN("k_ypass", st, fb, k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+      OFDFT_RUN("k_xgspace", st, fb, k_xgspace<T><<<dim3(grid_x, 1), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
+      OFDFT_RUN("k_ypass", st, fb, k_ypass<T, 1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+    }
+    TV* pe = pt + (size_t)std::max(grid_x, nh) * 3 * 4;
+    FinArgs<T> fa{pt, 0, pe, 0, res_d};
+    EpiArgs<T> ea{3, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)Te, (T)1, (T)0, cs.terms, out, pe, fa,
+                  counters + 0};
+    OFDFT_RUN("k_zinv_epi", st, (double)NH * sizeof(C) + (double)N * sizeof(T), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+    return OFDFT_OK;
+  }
+
   // From the 12 raw sums in res_h[0..11] (see finalize_eval) to
   // res_h: 0 F_TF 1 E_vW 2 E_NL 3 E_H 4 E_loc 5 E_xc 6 E_ion 7 F_total 8 N_e
   // 9 mu 10 residual 11 slope <g, d> 12 int v_rest n 13 nonfinite count.
@@ -630,15 +675,15 @@ class Engine : public IEngine {
     return OFDFT_OK;
   }
 
-  // d = sum_i c_i V_i; returns <d,d>, <d,g>, <d,psi> (times dV)
-  int lincomb(const VecList<T>& terms, double* dd, double* dg, double* dpsi, cudaStream_t st) {
+  // out = sum_i c_i V_i; returns <out,out>, <out,g>, <out,psi> (times dV)
+  int lincomb(const VecList<T>& terms, T* out, double* dd, double* dg, double* dpsi, cudaStream_t st) {
     VecList<T> xl = terms;
     const int nv = terms.nv;
     xl.v[nv] = g; xl.v[nv + 1] = psi;
     xl.nv = nv + 2;
     OFDFT_RUN("k_lincomb", st, (double)(nv + 3) * N * sizeof(T),
               k_lincomb<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(kMaxLin - 1), nv + 2), st>>>(
-                  xl, nv, d, N, partials, counters + 2, res_d + 16));
+                  xl, nv, out, N, partials, counters + 2, res_d + 16));
     int rc;
     if ((rc = read_results(st))) return rc;
     *dd = res_h[16] * dV; *dg = res_h[17] * dV; *dpsi = res_h[18] * dV;
@@ -820,32 +865,47 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     if (kk > 0) {
       const int sl = ring.slot(kk - 1);
       gamma = sy(sl, sl) / yy(sl, sl);
-    } else {
-      t0 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
     }
-    for (int i = 0; i < kk; ++i) {
-      double yr = Yg[i];
-      for (int j = 0; j < kk; ++j) yr -= alpha[j] * yy(ring.slot(i), ring.slot(j));
-      yr *= gamma;
-      for (int j = 0; j < i; ++j) yr += (alpha[j] - beta[j]) * sy(ring.slot(j), ring.slot(i));
-      beta[i] = rho[i] * yr;
-    }
-    // d = -gamma g + gamma sum alpha_j y_j - sum (alpha_j - beta_j) s_j
-    VecList<T> vl{};
-    vl.nv = 0;
-    vl.v[vl.nv] = g; vl.c[vl.nv++] = -gamma;
-    for (int j = 0; j < kk; ++j) {
-      vl.v[vl.nv] = Yh[ring.slot(j)]; vl.c[vl.nv++] = gamma * alpha[j];
-      vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]);
-    }
-    double dd = 0, dg = 0, dpsi = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      if ((rc = lincomb(vl, &dd, &dg, &dpsi, st))) return rc;
-      if (dg < 0 || attempt == 1) break;
-      // not a descent direction: drop the history and restart along -g
+    // With the initial inverse Hessian H0 = gamma P (P the kinetic
+    // preconditioner), the middle of the two-loop recursion is r = gamma P q,
+    // q = g - sum alpha_j y_j: one linear combination, one preconditioning
+    // pass and the dots <y_i, P q> replace the scalar-only middle step.
+    double dd = 0, dg = 0, dpsi = 0, dq = 0;
+    auto direction = [&](int nk) -> int {
+      int e;
+      if (nk > 0) {
+        VecList<T> ql{};
+        ql.nv = 0;
+        ql.v[ql.nv] = g; ql.c[ql.nv++] = 1.0;
+        for (int j = 0; j < nk; ++j) { ql.v[ql.nv] = Yh[ring.slot(j)]; ql.c[ql.nv++] = -alpha[j]; }
+        if ((e = lincomb(ql, qv, &dq, &dq, &dq, st))) return e;
+        if ((e = precondition(qv, rv, st))) return e;
+        std::vector<const T*> Yl;
+        for (int j = 0; j < nk; ++j) Yl.push_back(Yh[ring.slot(j)]);
+        std::vector<double> yr0;
+        if ((e = gram(Yl, {rv}, yr0, st))) return e;
+        for (int i = 0; i < nk; ++i) {
+          double yr = gamma * yr0[i];
+          for (int j = 0; j < i; ++j) yr += (alpha[j] - beta[j]) * sy(ring.slot(j), ring.slot(i));
+          beta[i] = rho[i] * yr;
+        }
+      } else {
+        if ((e = precondition(g, rv, st))) return e;
+      }
+      // d = -gamma P q - sum (alpha_j - beta_j) s_j
+      VecList<T> vl{};
+      vl.nv = 0;
+      vl.v[vl.nv] = rv; vl.c[vl.nv++] = nk > 0 ? -gamma : -1.0;
+      for (int j = 0; j < nk; ++j) { vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]); }
+      if ((e = lincomb(vl, d, &dd, &dg, &dpsi, st))) return e;
+      if (nk == 0) t0 = 0.1 * std::sqrt(Qcur / std::max(dd, 1e-300));   // first step: 10% of |psi|
+      return OFDFT_OK;
+    };
+    if ((rc = direction(kk))) return rc;
+    if (!(dg < 0) && kk > 0) {
+      // not a descent direction: drop the history and restart along -P g
       ring.clear();
-      vl.nv = 1; vl.v[0] = g; vl.c[0] = -1.0;
-      t0 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
+      if ((rc = direction(0))) return rc;
     }
     if (!(dg < 0)) break;
     // --- strong-Wolfe line search along d
@@ -869,21 +929,19 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     rc = line_search(phi, F, dg, t0, o.c1, o.c2, 40, rel_noise, &acc, &lsev);
     if (rc == OFDFT_ERR_NOT_CONVERGED && kk > 0) {
       // failed along the quasi-Newton direction: drop the history and retry once
-      // along -g (scaled as a first step) before giving up
+      // along -P g (scaled as a first step) before giving up
       ring.clear();
-      VecList<T> v1{};
-      v1.nv = 1; v1.v[0] = g; v1.c[0] = -1.0;
-      if ((rc = lincomb(v1, &dd, &dg, &dpsi, st))) return rc;
+      if ((rc = direction(0))) return rc;
       if (dg < 0) {
-        const double t1 = 0.1 * std::sqrt(Qcur / std::max(gg, 1e-300));
         int lsev2 = 0;
-        rc = line_search(phi, F, dg, t1, o.c1, o.c2, 40, rel_noise, &acc, &lsev2);
+        rc = line_search(phi, F, dg, t0, o.c1, o.c2, 40, rel_noise, &acc, &lsev2);
         lsev += lsev2;
       }
     }
     if (trace)
-      std::fprintf(stderr, "ofdft it %4d F %.12f dphi0 %.3e t %.3e ls_evals %d status %d R %.3e hist %d\n", it,
-                   rc == OFDFT_OK ? acc.f : F, dg, acc.t, lsev, rc, lastE[10], ring.count);
+      std::fprintf(stderr, "ofdft it %4d F %.12f dphi0 %.3e t %.3e ls_evals %d status %d R %.3e hist %d"
+                   " gamma %.9e dd %.9e dpsi %.9e Q %.12e gg %.9e\n", it,
+                   rc == OFDFT_OK ? acc.f : F, dg, acc.t, lsev, rc, lastE[10], ring.count, gamma, dd, dpsi, Qcur, gg);
     if (rc == OFDFT_ERR_NOT_CONVERGED) break;
     if (rc) return rc;
     // --- accept: s = t d, y = g_t - g, psi += t d, g = g_t  (the last trial is the accepted one)

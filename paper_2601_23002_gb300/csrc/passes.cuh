@@ -334,6 +334,9 @@ template <typename T> struct GArgs {
   // [gridDim.y * gridDim.x][4]: E_H, E_loc, E_NL, E_vW(raw), as float-float
   // pairs (FP32 plans) or doubles
   typename TreeVal<T>::type* partials;
+  // non-null: the psi field is the minimiser's preconditioning pass, and its
+  // spectrum is multiplied by this table of p(m^2) instead (see minimize)
+  const T* prec;
 };
 
 // One block per (tile, field): blockIdx.y indexes the active fields.
@@ -410,6 +413,10 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
       const T k = g.K[m2];
       acc[2].add(w * Om * k * a2);
       o = mk<T>(k * vr, k * vi);
+    } else if (g.prec != nullptr) {
+      // preconditioning pass: P f = IFFT[p(G) f~] (no energies)
+      const T pg = g.prec[m2];
+      o = mk<T>(pg * vr, pg * vi);
     } else {
       acc[3].add(w * halfOm * G2 * a2);
       if (sp.merged) {
@@ -499,7 +506,9 @@ static __device__ void finalize_eval(const FinArgs<T>& f, typename TreeVal<T>::t
 // ---------------------------------------------------------------------------
 // 5. C2R along z + pointwise functional.
 template <typename T> struct EpiArgs {
-  int mode;              // 0: density given (write v); 1: psi + t d (write g')
+  int mode;              // 0: density given (write v); 1: psi + t d (write g');
+                         // 3: preconditioning pass (write the psi field's real
+                         // output to out; no functional, no sums)
   const T* rho;
   const T* psi;
   const T* d;
@@ -555,7 +564,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
     constexpr int E = 8 / sizeof(T);
     const int pieces = tot / E;
     const T* src0 = a.mode == 0 ? a.rho : a.psi;
-    for (int q = threadIdx.x; q < pieces; q += blockDim.x) {
+    for (int q = threadIdx.x; q < (a.mode == 3 ? 0 : pieces); q += blockDim.x) {
       cp_async<8>(pin + q * E, src0 + off + q * E, true);
       if (a.mode != 0) cp_async<8>(pin + (size_t)Rfull * n + q * E, a.d + off + q * E, true);
     }
@@ -590,6 +599,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
     __syncthreads();
   }
   // pointwise functional
+  if (a.mode == 3) {
+    // every block takes this branch: no partial sums, no final reduction
+    const T* fP = realf[2];
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) a.out[off + q] = fP[q];
+    return;
+  }
   const bool has_n = sp.s[0] != nullptr, has_na = sp.s[1] != nullptr, has_psi = sp.s[2] != nullptr;
   const T* fH = realf[0];
   const T* fK = realf[1];

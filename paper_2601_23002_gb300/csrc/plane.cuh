@@ -170,6 +170,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
       const T k = g.K[m2];
       acc[2].add(w * Om * k * a2);
       o = mk<T>(k * vr, k * vi);
+    } else if (g.prec != nullptr) {
+      // preconditioning pass: P f = IFFT[p(G) f~] (no energies)
+      const T pg = g.prec[m2];
+      o = mk<T>(pg * vr, pg * vi);
     } else {
       acc[3].add(w * halfOm * G2 * a2);
       if (sp.merged) {
