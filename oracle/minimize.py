@@ -11,6 +11,12 @@ int a b = dV sum a b.  Initial state: the uniform density.
 
 Convergence: |dF| / N_ion below tol_F for 3 consecutive iterations and the
 Euler-Lagrange residual R = (int n (v - mu)^2 / N_e)^(1/2) below tol_R.
+
+Optional preconditioning (precond_c = c): the two-loop recursion starts from
+H0 = gamma P instead of gamma I, with P f = IFFT[c / (c + G^2/2) f~], the
+inverse of the vW kinetic operator shifted by c; the first direction is -P g.
+Any symmetric positive-definite H0 leaves the minimum unchanged; the tests
+check that both forms reach the same one.
 """
 from __future__ import annotations
 
@@ -103,11 +109,17 @@ def line_search(phi, phi0, dphi0, t0, c1=1e-4, c2=0.9, max_evals=30):
 
 
 def lbfgs(functional, psi0=None, m=8, c1=1e-4, c2=0.9, tol_F=1e-6, tol_R=1e-4,
-          max_iter=1000, verbose=False) -> MinResult:
+          max_iter=1000, verbose=False, precond_c=None) -> MinResult:
     """L-BFGS on psi (see module docstring).  functional.evaluate_psi(psi)
     returns (energies, gradient, rho)."""
     F = functional
     dV = F.dV
+    if precond_c is None:
+        P = lambda v: v
+    else:
+        from .functional import fft3, ifft3
+        pg = precond_c / (precond_c + 0.5 * F.G2)
+        P = lambda v: ifft3(fft3(v) * pg)
     n_ion = float(len(F.cell.Z))
     dot = lambda a, b: dV * float(np.sum(a * b))
     psi = np.full((F.n,) * 3, math.sqrt(F.nbar)) if psi0 is None else np.array(psi0, float)
@@ -125,13 +137,14 @@ def lbfgs(functional, psi0=None, m=8, c1=1e-4, c2=0.9, tol_F=1e-6, tol_R=1e-4,
             a = r * dot(s, q)
             alphas.append(a)
             q -= a * y
+        z = P(q)
         if S:
             gamma = dot(S[-1], Y[-1]) / dot(Y[-1], Y[-1])
             t0 = 1.0
         else:
             gamma = 1.0
-            t0 = 0.1 * math.sqrt(dot(psi, psi) / max(dot(g, g), 1e-300))
-        z = gamma * q
+            t0 = 0.1 * math.sqrt(dot(psi, psi) / max(dot(z, z), 1e-300))
+        z = gamma * z
         for (s, y, r), a in zip(zip(S, Y, RHO), reversed(alphas)):
             b = r * dot(y, z)
             z += (a - b) * s
@@ -139,9 +152,9 @@ def lbfgs(functional, psi0=None, m=8, c1=1e-4, c2=0.9, tol_F=1e-6, tol_R=1e-4,
         dphi0 = dot(g, d)
         if dphi0 >= 0:            # not a descent direction: restart from steepest descent
             S, Y, RHO = [], [], []
-            d = -g
+            d = -P(g)
             dphi0 = dot(g, d)
-            t0 = 0.1 * math.sqrt(dot(psi, psi) / max(dot(g, g), 1e-300))
+            t0 = 0.1 * math.sqrt(dot(psi, psi) / max(dot(d, d), 1e-300))
 
         def phi(t):
             x = psi + t * d

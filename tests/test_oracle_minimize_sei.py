@@ -46,6 +46,19 @@ def test_minimum_independent_of_optimizer_constants(small_min):
     assert np.linalg.norm(r.rho - r0.rho) / np.linalg.norm(r0.rho) < 1e-6
 
 
+def test_preconditioned_minimiser_reaches_the_same_minimum(small_min):
+    # H0 = gamma P with the kinetic preconditioner P changes the path, not the
+    # minimum; on this cell it also needs fewer iterations
+    c, F0, r0 = small_min
+    F = Functional(c)
+    kF = (3 * math.pi ** 2 * c.n_electrons / c.volume) ** (1 / 3)
+    r = lbfgs(F, precond_c=0.5 * kF ** 2, tol_F=1e-11, tol_R=1e-8, max_iter=400)
+    assert r.converged
+    assert abs(r.energies["total"] - r0.energies["total"]) / c.n_ion < 1e-10
+    assert np.linalg.norm(r.rho - r0.rho) / np.linalg.norm(r0.rho) < 1e-6
+    assert r.iterations < r0.iterations
+
+
 def test_sei_uniform_is_zero():
     c = random_cell(21, 8, 1.0, 1.5, 1.0, 16)
     q, s = sei_shells(np.full((16,) * 3, c.n_electrons / c.volume), c.pos, c.L, c.n_electrons, 40)
