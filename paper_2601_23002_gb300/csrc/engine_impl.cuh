@@ -501,13 +501,22 @@ class Engine : public IEngine {
     const int full = S_out != nullptr;
     // rows are also kept out to |m|^2 = 600 for the S_ei shells
     const double g2rows = std::max(g2max, (2.0 * kPi / L) * (2.0 * kPi / L) * 600.0);
-    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<n * n, 128, 0, st>>>(phases, Z_d, nion, n, L, cs.rc, eta, g2rows, full, Sg, vloc, partials));
+    // without the full S(G), only rows with |mx|, |my| <= mlim can reach g2rows:
+    // zero everything, then compute that square of rows
+    int mlim = (int)std::floor(std::sqrt(g2rows) / (2.0 * kPi / L));
+    if (full || mlim > n / 2 - 1) mlim = -1;
+    const int nrows = mlim < 0 ? n * n : (2 * mlim + 1) * (2 * mlim + 1);
+    if (mlim >= 0) {
+      OFDFT_CK(cudaMemsetAsync(Sg, 0, NH * sizeof(C), st));
+      OFDFT_CK(cudaMemsetAsync(vloc, 0, NH * sizeof(C), st));
+    }
+    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<nrows, 128, 0, st>>>(phases, Z_d, nion, n, L, cs.rc, eta, g2rows, full, mlim, Sg, vloc, partials));
     int rc;
-    if ((rc = sum_partials(n * n, 1, 0, st))) return rc;
+    if ((rc = sum_partials(nrows, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
     const int nimg = (int)std::ceil(rcut / L) + 1;
-    const long npair = (long)nion * nion;
-    const int gb = (int)std::min<long>(2048, (npair + 255) / 256);
+    const long ncomb = (long)nion * nion * (2 * nimg + 1) * (2 * nimg + 1) * (2 * nimg + 1);
+    const int gb = (int)std::min<long>(std::min<long>(2048, 4L * nsm), (ncomb + 255) / 256);
     OFDFT_RUN("k_ewald_real", st, (double)nion * 32, k_ewald_real<<<gb, 256, 0, st>>>(pos_d, Z_d, nion, L, eta, rcut, nimg, partials));
     if ((rc = sum_partials(gb, 1, 1, st))) return rc;
     OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -675,7 +684,8 @@ class Engine : public IEngine {
     return OFDFT_OK;
   }
 
-  // out = sum_i c_i V_i; returns <out,out>, <out,g>, <out,psi> (times dV)
+  // out = sum_i c_i V_i; returns <out,out>, <out,g>, <out,psi> (times dV);
+  // with dd == nullptr the dots are not read back (no host synchronisation)
   int lincomb(const VecList<T>& terms, T* out, double* dd, double* dg, double* dpsi, cudaStream_t st) {
     VecList<T> xl = terms;
     const int nv = terms.nv;
@@ -684,6 +694,7 @@ class Engine : public IEngine {
     OFDFT_RUN("k_lincomb", st, (double)(nv + 3) * N * sizeof(T),
               k_lincomb<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(kMaxLin - 1), nv + 2), st>>>(
                   xl, nv, out, N, partials, counters + 2, res_d + 16));
+    if (!dd) return OFDFT_OK;
     int rc;
     if ((rc = read_results(st))) return rc;
     *dd = res_h[16] * dV; *dg = res_h[17] * dV; *dpsi = res_h[18] * dV;
@@ -870,7 +881,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     // preconditioner), the middle of the two-loop recursion is r = gamma P q,
     // q = g - sum alpha_j y_j: one linear combination, one preconditioning
     // pass and the dots <y_i, P q> replace the scalar-only middle step.
-    double dd = 0, dg = 0, dpsi = 0, dq = 0;
+    double dd = 0, dg = 0, dpsi = 0;
     auto direction = [&](int nk) -> int {
       int e;
       if (nk > 0) {
@@ -878,7 +889,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
         ql.nv = 0;
         ql.v[ql.nv] = g; ql.c[ql.nv++] = 1.0;
         for (int j = 0; j < nk; ++j) { ql.v[ql.nv] = Yh[ring.slot(j)]; ql.c[ql.nv++] = -alpha[j]; }
-        if ((e = lincomb(ql, qv, &dq, &dq, &dq, st))) return e;
+        if ((e = lincomb(ql, qv, nullptr, nullptr, nullptr, st))) return e;
         if ((e = precondition(qv, rv, st))) return e;
         std::vector<const T*> Yl;
         for (int j = 0; j < nk; ++j) Yl.push_back(Yh[ring.slot(j)]);

@@ -37,7 +37,7 @@ static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n
 template <typename T>
 __global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, const double* __restrict__ Z,
                                                 int n_ion, int n, double L, double rc, double eta_ew,
-                                                double g2max, int full,
+                                                double g2max, int full, int mlim,
                                                 cplx<T>* __restrict__ S_out, cplx<T>* __restrict__ vloc,
                                                 double* __restrict__ ew_partial) {
   constexpr int CH = 128;
@@ -45,9 +45,18 @@ __global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, 
   __shared__ T szz[CH];
   __shared__ double red[32];
   const int nh = n / 2 + 1;
-  const int kx = blockIdx.x / n, ky = blockIdx.x % n;
-  const int mx = kx <= n / 2 - 1 ? kx : kx - n;
-  const int my = ky <= n / 2 - 1 ? ky : ky - n;
+  // mlim < 0: one block per row (kx, ky) of the grid; mlim >= 0: one block per
+  // row with |mx|, |my| <= mlim (the caller has zeroed the other rows)
+  int kx, ky, mx, my;
+  if (mlim < 0) {
+    kx = blockIdx.x / n; ky = blockIdx.x % n;
+    mx = kx <= n / 2 - 1 ? kx : kx - n;
+    my = ky <= n / 2 - 1 ? ky : ky - n;
+  } else {
+    const int side = 2 * mlim + 1;
+    mx = (int)(blockIdx.x / side) - mlim; my = (int)(blockIdx.x % side) - mlim;
+    kx = mx < 0 ? mx + n : mx; ky = my < 0 ? my + n : my;
+  }
   const double tp = 2.0 * kPi / L;
   const double Omega = L * L * L;
   const double g2row = tp * tp * (double)(mx * mx + my * my);
@@ -107,22 +116,29 @@ __global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, 
 
 // ---------------------------------------------------------------------------
 // Ewald: real-space pair sum (all pairs I, J and lattice images within rcut).
+// One (pair, image) per thread step, so that the FP64 work (the squared
+// distance for every combination, sqrt and erfc inside the cutoff) spreads
+// over the whole GPU instead of one image loop per pair.
 static __global__ void k_ewald_real(const double* __restrict__ pos, const double* __restrict__ Z, int n_ion,
                              double L, double eta, double rcut, int nimg, double* __restrict__ partial) {
   __shared__ double red[32];
   double acc = 0;
-  const long npair = (long)n_ion * n_ion;
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += (long)gridDim.x * blockDim.x) {
+  const int side = 2 * nimg + 1;
+  const long nim3 = (long)side * side * side;
+  const long tot = (long)n_ion * n_ion * nim3;
+  const double rc2 = rcut * rcut;
+  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (long)gridDim.x * blockDim.x) {
+    const long p = q / nim3;
+    const int im = (int)(q - p * nim3);
     const int I = (int)(p / n_ion), J = (int)(p % n_ion);
-    const double dx = pos[I * 3] - pos[J * 3], dy = pos[I * 3 + 1] - pos[J * 3 + 1],
-                 dz = pos[I * 3 + 2] - pos[J * 3 + 2];
-    for (int a = -nimg; a <= nimg; ++a)
-      for (int b = -nimg; b <= nimg; ++b)
-        for (int c = -nimg; c <= nimg; ++c) {
-          const double x = dx + a * L, y = dy + b * L, z = dz + c * L;
-          const double r = sqrt(x * x + y * y + z * z);
-          if (r > 1e-12 && r < rcut) acc += 0.5 * Z[I] * Z[J] * erfc(eta * r) / r;
-        }
+    const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
+    const double x = pos[I * 3] - pos[J * 3] + a * L, y = pos[I * 3 + 1] - pos[J * 3 + 1] + b * L,
+                 z = pos[I * 3 + 2] - pos[J * 3 + 2] + c * L;
+    const double r2 = x * x + y * y + z * z;
+    if (r2 > 1e-24 && r2 < rc2) {
+      const double r = sqrt(r2);
+      acc += 0.5 * Z[I] * Z[J] * erfc(eta * r) / r;
+    }
   }
   double v[1] = {acc}, out[1];
   block_sum<1>(v, red, out);
