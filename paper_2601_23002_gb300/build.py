@@ -1,7 +1,8 @@
 """Builds the CUDA library libofdft_gb300.so in-tree (sm_103a).
 
-The three translation units (C-ABI layer, FP32 engine, FP64 engine) are
-compiled in parallel with nvcc and linked into
+The translation units (C-ABI layer, FP32 and FP64 engines, the plane-pass
+kernels of each precision, the allocation-free entry point) are compiled in
+parallel with nvcc and linked into
 paper_2601_23002_gb300/_build/libofdft_gb300.so.
 """
 from __future__ import annotations
@@ -16,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libofdft_gb300.so")
-SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "plane_f32.cu", "plane_f64.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

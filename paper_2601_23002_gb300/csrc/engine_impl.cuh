@@ -95,6 +95,7 @@ class Engine : public IEngine {
   bool planes = false;
   size_t smem_pl = 0;
   int* rev_d = nullptr;      // position -> frequency of the in-place transforms
+  PlaneKernel<T> plane_kern = nullptr;   // k_plane compiled for this grid's radices
   C* vloc_pl = nullptr;      // V_loc in plane layout and position order
   C* spec[3] = {nullptr, nullptr, nullptr};
   T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
@@ -255,6 +256,7 @@ class Engine : public IEngine {
       return OFDFT_ERR_INVALID;
     }
     pn.n = n; ph.n = h;
+    if (planes) plane_kern = plane_kernel<T>(radix_mask(pn));
     int rc;
     // twiddles
     std::vector<C> twn(n), twh(h);
@@ -400,7 +402,7 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
     if ((rc = raise((const void*)k_xpass<T, -1>, smem_xp))) return rc;
-    if (planes && (rc = raise((const void*)k_plane<T>, smem_pl))) return rc;
+    if (planes && (rc = raise((const void*)plane_kern, smem_pl))) return rc;
     const size_t sring = StreamCfg<T>::ring_bytes(3, 17);   // largest ring any streaming launch uses
     if ((rc = raise((const void*)k_gram<T, 1, 3>, sring))) return rc;
     if ((rc = raise((const void*)k_gram<T, 2, 3>, sring))) return rc;
@@ -550,7 +552,7 @@ class Engine : public IEngine {
     if (sp.nact > 0) {
       OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
       if (planes) {
-        OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_plane<T><<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
+        OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), plane_kern<<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
         g_rows = nh * sp.nact;
       } else {
         OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
@@ -589,7 +591,7 @@ class Engine : public IEngine {
     const double fb = 2.0 * NH * sizeof(C);
     OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
     if (planes) {
-      OFDFT_RUN("k_plane", st, fb, k_plane<T><<<dim3(nh, 1), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
+      OFDFT_RUN("k_plane", st, fb, plane_kern<<<dim3(nh, 1), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
     } else {
       OFDFT_RUN("k_ypass", st, fb, k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
       OFDFT_RUN("k_xgspace", st, fb, k_xgspace<T><<<dim3(grid_x, 1), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));

@@ -66,28 +66,43 @@ __device__ __forceinline__ void ip_stage(cplx<T>* __restrict__ a, int n, int Lsu
   }
 }
 
-template <typename T, int DIR>
+// Stage dispatch over the radices in MASK (bit r set: radix r compiled in).
+// A kernel holds only the codelets its grid size uses: with all eleven
+// radices inlined, a block of 16 warps stalled on instruction fetch after
+// every stage barrier.
+constexpr unsigned kAllRadices = (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 8) |
+                                 (1u << 9) | (1u << 10) | (1u << 12) | (1u << 15) | (1u << 16);
+template <typename T, int DIR, unsigned MASK>
 __device__ __forceinline__ void ip_stage_any(int R, cplx<T>* a, int n, int Lsub, int ld_elem, int ld_line, int lines,
                                              bool line_fastest, const cplx<T>* tw) {
-  switch (R) {
-    case 2: ip_stage<T, 2, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 3: ip_stage<T, 3, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 4: ip_stage<T, 4, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 5: ip_stage<T, 5, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 6: ip_stage<T, 6, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 8: ip_stage<T, 8, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 9: ip_stage<T, 9, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 10: ip_stage<T, 10, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 12: ip_stage<T, 12, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 15: ip_stage<T, 15, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    case 16: ip_stage<T, 16, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); break;
-    default: break;
+#define OFDFT_IP_CASE(RR)                                                              \
+  if constexpr (((MASK >> RR) & 1u) != 0) {                                           \
+    if (R == RR) { ip_stage<T, RR, DIR>(a, n, Lsub, ld_elem, ld_line, lines, line_fastest, tw); return; } \
   }
+  OFDFT_IP_CASE(16)
+  OFDFT_IP_CASE(8)
+  OFDFT_IP_CASE(12)
+  OFDFT_IP_CASE(10)
+  OFDFT_IP_CASE(9)
+  OFDFT_IP_CASE(6)
+  OFDFT_IP_CASE(5)
+  OFDFT_IP_CASE(4)
+  OFDFT_IP_CASE(3)
+  OFDFT_IP_CASE(2)
+  OFDFT_IP_CASE(15)
+#undef OFDFT_IP_CASE
+}
+
+// bit mask of the radices of a plan
+inline unsigned radix_mask(const FftPlan1& p) {
+  unsigned m = 0;
+  for (int i = 0; i < p.npass; ++i) m |= 1u << p.radix[i];
+  return m;
 }
 
 // Forward (DIR < 0, stages in plan order) or inverse (DIR > 0, reverse order)
 // transforms of all n lines of the plane along one axis.  Ends with a barrier.
-template <typename T, int DIR>
+template <typename T, int DIR, unsigned MASK>
 __device__ __forceinline__ void ip_fft_axis(cplx<T>* a, const FftPlan1& p, int ld_elem, int ld_line, bool rows,
                                             const cplx<T>* tw) {
   const int n = p.n;
@@ -100,7 +115,7 @@ __device__ __forceinline__ void ip_fft_axis(cplx<T>* a, const FftPlan1& p, int l
     // along rows (unit stride) keep unit-stride runs when they span a warp;
     // otherwise put consecutive threads on consecutive lines
     const bool line_fastest = !rows || Ls[s] / R < 32;
-    ip_stage_any<T, DIR>(R, a, n, Ls[s], ld_elem, ld_line, n, line_fastest, tw);
+    ip_stage_any<T, DIR, MASK>(R, a, n, Ls[s], ld_elem, ld_line, n, line_fastest, tw);
     __syncthreads();
   }
 }
@@ -111,7 +126,7 @@ constexpr int kPlaneThreads = 512;
 // layout: field f's plane kz is sp.s[f] + kz * n * n, row kx, column ky.
 // vloc (if given) is in plane layout and position order: entry (kz, px, py)
 // is V_loc(kx = rev[px], ky = rev[py], kz).
-template <typename T>
+template <typename T, unsigned MASK>
 __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs<T> g, FftPlan1 pn,
                                                             const int* __restrict__ rev_g,
                                                             const cplx<T>* __restrict__ tw_g) {
@@ -132,8 +147,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
   for (int q = threadIdx.x; q < n; q += blockDim.x) { tw[q] = tw_g[q]; rev[q] = rev_g[q]; }
   cp_async_wait<0>();
   __syncthreads();
-  ip_fft_axis<T, -1>(a, pn, 1, pitch, true, tw);       // along ky (rows)
-  ip_fft_axis<T, -1>(a, pn, pitch, 1, false, tw);      // along kx (columns)
+  ip_fft_axis<T, -1, MASK>(a, pn, 1, pitch, true, tw);       // along ky (rows)
+  ip_fft_axis<T, -1, MASK>(a, pn, pitch, 1, false, tw);      // along kx (columns)
   // G-space terms (same arithmetic as the x/G-space pass of the tiled path)
   const T tp2 = g.tp2, invN = g.invN, Om = g.Om, halfOm = g.halfOm, fourpi = (T)(4.0 * kPi);
   const T g2cut = g.g2cut_loc;
@@ -188,8 +203,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
     *cell = o;
   }
   __syncthreads();
-  ip_fft_axis<T, 1>(a, pn, pitch, 1, false, tw);       // inverse along kx
-  ip_fft_axis<T, 1>(a, pn, 1, pitch, true, tw);        // inverse along ky
+  ip_fft_axis<T, 1, MASK>(a, pn, pitch, 1, false, tw);       // inverse along kx
+  ip_fft_axis<T, 1, MASK>(a, pn, 1, pitch, true, tw);        // inverse along ky
   for (int q = threadIdx.x; q < nn; q += blockDim.x) {
     const int r = qdiv(q, n, Mn), c = q - r * n;
     gpl[q] = a[r * pitch + c];
@@ -197,6 +212,13 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
   const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
   block_sum_tree_raw<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
 }
+
+// The plane kernel compiled for a plan's radices (instantiated in
+// plane_f32.cu / plane_f64.cu for the radix sets of the supported grids; any
+// other set gets the kernel with every radix).
+template <typename T>
+using PlaneKernel = void (*)(Spectra<T>, GArgs<T>, FftPlan1, const int*, const cplx<T>*);
+template <typename T> PlaneKernel<T> plane_kernel(unsigned mask);
 
 // One-time reorder of V_loc from the tiled layout [kx][ky][kz] into plane
 // layout and position order: dst[(kz n + px) n + py] = src[(rev[px] n + rev[py]) nh + kz].
