@@ -341,11 +341,17 @@ class Engine : public IEngine {
     }
     OFDFT_RUN("k_convert_table", st, (double)nm2 * (8 + sizeof(T)), k_convert_table<T><<<(nm2 + 255) / 256, 256, 0, st>>>(Kd, Kt, nm2));
     {
-      // kinetic preconditioner of the minimiser: p(G) = c / (c + G^2/2) with
-      // c = k_F^2/2 of the mean density (the scale below which the Thomas-Fermi
-      // response, not the vW kinetic term, sets the curvature)
+      // kinetic preconditioner of the minimiser: p(G) = c / (c + G^2/2).  The
+      // psi-Hessian of the Thomas-Fermi term at the mean density is about
+      // 2 mu + 4 n dmu/dn, ~4 E_F degenerate and ~4 T classical, so below
+      // G^2/2 ~ 4 (E_F + T) it, not the vW term, sets the curvature.
+      // c = 4 (E_F + T) was the best of a scan (0.5-12) over the 128^3 cell,
+      // 64 batched cells and 60 serving cells (11, 20.2 and 20.1 evaluations
+      // on average); OFDFT_PREC_C replaces the factor 4, for such studies.
       const double kF = std::cbrt(3.0 * kPi * kPi * nbar);
-      const double c = 0.5 * kF * kF;
+      double cfac = 4.0;
+      if (const char* ev = std::getenv("OFDFT_PREC_C")) cfac = std::atof(ev) > 0 ? std::atof(ev) : cfac;
+      const double c = cfac * (0.5 * kF * kF + Te);
       const double tp2d = (2.0 * kPi / L) * (2.0 * kPi / L);
       std::vector<T> ph_(nm2);
       for (int m2 = 0; m2 < nm2; ++m2) ph_[m2] = (T)(c / (c + 0.5 * tp2d * m2));
