@@ -99,8 +99,11 @@ class Engine : public IEngine {
   C* vloc_pl = nullptr;      // V_loc in plane layout and position order
   C* spec[3] = {nullptr, nullptr, nullptr};
   T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
-  // preconditioned two-loop recursion: q, P q and the table p(m^2)
-  T *qv = nullptr, *rv = nullptr, *precT = nullptr;
+  // preconditioned two-loop recursion: P g (current and previous g), P y of
+  // the history pairs, and the table p(m^2)
+  T* pgv[2] = {nullptr, nullptr};
+  T* PYh[kMaxMem] = {};
+  T* precT = nullptr;
   T* Sh[kMaxMem] = {};
   T* Yh[kMaxMem] = {};
   double* partials = nullptr;
@@ -237,7 +240,7 @@ class Engine : public IEngine {
     size_t b = 0;
     b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
     if (planes) b += NH * sizeof(C);                         // vloc in plane order
-    b += (6 + 2 * (size_t)m_max) * N * sizeof(T);            // psi d g gp q Pq + history
+    b += (6 + 3 * (size_t)m_max) * N * sizeof(T);            // psi d g gp, P g x2, history s y P y
     b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
     b += (size_t)(n + h) * sizeof(C);
     return b;
@@ -301,11 +304,12 @@ class Engine : public IEngine {
     if ((rc = alloc(&d, N))) return rc;
     if ((rc = alloc(&g, N))) return rc;
     if ((rc = alloc(&gp, N))) return rc;
-    if ((rc = alloc(&qv, N))) return rc;
-    if ((rc = alloc(&rv, N))) return rc;
+    if ((rc = alloc(&pgv[0], N))) return rc;
+    if ((rc = alloc(&pgv[1], N))) return rc;
     for (int i = 0; i < m_max; ++i) {
       if ((rc = alloc(&Sh[i], N))) return rc;
       if ((rc = alloc(&Yh[i], N))) return rc;
+      if ((rc = alloc(&PYh[i], N))) return rc;
     }
     const int nm2 = 3 * h * h + 1;
     if ((rc = alloc(&Kd, nm2))) return rc;
@@ -418,6 +422,8 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_gram<T, 2, 2>, sring))) return rc;
     if ((rc = raise((const void*)k_gram<T, 3, 2>, sring))) return rc;
     if ((rc = raise((const void*)k_gram<T, 4, 2>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 5, 3>, sring))) return rc;
+    if ((rc = raise((const void*)k_gram<T, 5, 2>, sring))) return rc;
     if ((rc = raise((const void*)k_lincomb<T>, sring))) return rc;
     if ((rc = raise((const void*)k_accept<T>, sring))) return rc;
     return OFDFT_OK;
@@ -585,7 +591,7 @@ class Engine : public IEngine {
 
   // out = P in = IFFT[p(G) FFT(in)/N]: the psi-field transform chain on a
   // plain vector with the G-space factor p(m^2) (GArgs::prec, EpiArgs mode 3)
-  int precondition(const T* in, T* out, cudaStream_t st) {
+  int precondition(const T* in, T* out, cudaStream_t st, const T* pold = nullptr, T* pyout = nullptr) {
     Spectra<T> sp{};
     sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = planes ? 1 : 0;
     ProArgs<T> pa{1, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)0};
@@ -606,7 +612,7 @@ class Engine : public IEngine {
     TV* pe = pt + (size_t)std::max(grid_x, nh) * 3 * 4;
     FinArgs<T> fa{pt, 0, pe, 0, res_d};
     EpiArgs<T> ea{3, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)Te, (T)1, (T)0, cs.terms, out, pe, fa,
-                  counters + 0};
+                  counters + 0, pold, pyout};
     OFDFT_RUN("k_zinv_epi", st, (double)NH * sizeof(C) + (double)N * sizeof(T), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     return OFDFT_OK;
   }
@@ -661,8 +667,9 @@ class Engine : public IEngine {
     if ((size_t)nv * nw > 104 || nw > kMaxW) { set_error("gram: too many vectors"); return OFDFT_ERR_INVALID; }
     out.assign((size_t)nv * nw, 0.0);
     // every chunk's last block writes its columns to res_d[16 + c0 * nw ...]
-    for (int c0 = 0; c0 < nv; c0 += kMaxV) {
-      const int cn = std::min(kMaxV, nv - c0);
+    const int chunk = std::min(kMaxV, kMaxLin - nw);      // a launch streams cn + nw <= kMaxLin vectors
+    for (int c0 = 0; c0 < nv; c0 += chunk) {
+      const int cn = std::min(chunk, nv - c0);
       VecList<T> xl{}; xl.nv = cn + nw;
       for (int i = 0; i < cn; ++i) xl.v[i] = V[c0 + i];
       for (int j = 0; j < nw; ++j) xl.v[cn + j] = W[j];
@@ -676,10 +683,12 @@ class Engine : public IEngine {
         case 2 * 8 + 3: launch(k_gram<T, 2, 3>); break;
         case 3 * 8 + 3: launch(k_gram<T, 3, 3>); break;
         case 4 * 8 + 3: launch(k_gram<T, 4, 3>); break;
+        case 5 * 8 + 3: launch(k_gram<T, 5, 3>); break;
         case 1 * 8 + 2: launch(k_gram<T, 1, 2>); break;
         case 2 * 8 + 2: launch(k_gram<T, 2, 2>); break;
         case 3 * 8 + 2: launch(k_gram<T, 3, 2>); break;
         case 4 * 8 + 2: launch(k_gram<T, 4, 2>); break;
+        case 5 * 8 + 2: launch(k_gram<T, 5, 2>); break;
         default: set_error("gram: no kernel for this list"); return OFDFT_ERR_INVALID;
       }
       prof.end(st);
@@ -818,11 +827,19 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
   OFDFT_RUN("k_project", st, 3.0 * N * sizeof(T), k_project<T><<<grid_vec, kThreads, 0, st>>>(g, gp, psi, Ne / Qcur, res_h[9], N));
   double mu_ref = res_h[9];   // reference chemical potential for g' (mu of the last accepted point)
 
+  // P g of the current g (pgv[pcur]); the previous one is kept until the next
+  // preconditioning pass has formed P y = P g_new - P g_old
+  int pcur = 0;
+  if ((rc = precondition(g, pgv[pcur], st))) return rc;
+
   Ring ring; ring.m = m;
   std::vector<double> SY((size_t)kMaxMem * kMaxMem, 0.0), YY((size_t)kMaxMem * kMaxMem, 0.0);
+  std::vector<double> YPY((size_t)kMaxMem * kMaxMem, 0.0);    // <y_a, P y_b>
   std::vector<double> Sgv(kMaxMem, 0.0), Ygv(kMaxMem, 0.0);   // <s_slot, g>, <y_slot, g> for the current g
+  std::vector<double> YPg(kMaxMem, 0.0);                      // <y_slot, P g>
   auto sy = [&](int a, int b) -> double& { return SY[(size_t)a * kMaxMem + b]; };
   auto yy = [&](int a, int b) -> double& { return YY[(size_t)a * kMaxMem + b]; };
+  auto ypy = [&](int a, int b) -> double& { return YPY[(size_t)a * kMaxMem + b]; };
   double gg = 0;
   {
     std::vector<double> d0;
@@ -835,20 +852,22 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
   bool converged = false;
   for (it = 1; it <= o.max_iter; ++it) {
     if (new_slot >= 0) {
-      // the accepted pair's own dots came from k_accept (res 120..125); the
-      // older pairs are dotted with [g, s_new, y_new] in one pass
+      // P g of the new gradient, and P y_new = P g_new - P g_old on the way
+      const int pnew = 1 - pcur;
+      if ((rc = precondition(g, pgv[pnew], st, pgv[pcur], PYh[new_slot]))) return rc;
+      pcur = pnew;
+      // the accepted pair's own dots came from k_accept (res 120..125); one
+      // pass dots [older s, older y, y_new] with [g, P g, s_new, y_new, P y_new]
       std::vector<int> old;
       for (int i = 0; i < ring.count; ++i)
         if (ring.slot(i) != new_slot) old.push_back(ring.slot(i));
+      const int no = (int)old.size();
+      std::vector<const T*> V;
+      for (int sl : old) V.push_back(Sh[sl]);
+      for (int sl : old) V.push_back(Yh[sl]);
+      V.push_back(Yh[new_slot]);
       std::vector<double> cross;
-      if (!old.empty()) {
-        std::vector<const T*> V;
-        for (int sl : old) V.push_back(Sh[sl]);
-        for (int sl : old) V.push_back(Yh[sl]);
-        if ((rc = gram(V, {g, Sh[new_slot], Yh[new_slot]}, cross, st))) return rc;
-      } else {
-        OFDFT_CK(cudaStreamSynchronize(st));
-      }
+      if ((rc = gram(V, {g, pgv[pcur], Sh[new_slot], Yh[new_slot], PYh[new_slot]}, cross, st))) return rc;
       const double* a = res_h + 120;
       sy(new_slot, new_slot) = a[0] * dV;
       yy(new_slot, new_slot) = a[1] * dV;
@@ -856,27 +875,32 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       gg = a[3] * dV;
       Sgv[new_slot] = a[4] * dV;
       Ygv[new_slot] = a[5] * dV;
-      const int no = (int)old.size();
+      auto X = [&](int row, int col) { return cross[(size_t)row * 5 + col]; };   // cols: g, Pg, s_new, y_new, Py_new
       for (int i = 0; i < no; ++i) {
         const int si = old[i];
-        Sgv[si] = cross[(size_t)i * 3 + 0];
-        sy(si, new_slot) = cross[(size_t)i * 3 + 2];            // <s_i, y_new>
-        Ygv[si] = cross[(size_t)(no + i) * 3 + 0];
-        sy(new_slot, si) = cross[(size_t)(no + i) * 3 + 1];     // <s_new, y_i>
-        yy(si, new_slot) = cross[(size_t)(no + i) * 3 + 2];     // <y_i, y_new>
-        yy(new_slot, si) = yy(si, new_slot);
+        Sgv[si] = X(i, 0);
+        sy(si, new_slot) = X(i, 3);                 // <s_i, y_new>
+        Ygv[si] = X(no + i, 0);
+        YPg[si] = X(no + i, 1);
+        sy(new_slot, si) = X(no + i, 2);            // <s_new, y_i>
+        yy(si, new_slot) = yy(new_slot, si) = X(no + i, 3);
+        ypy(si, new_slot) = ypy(new_slot, si) = X(no + i, 4);
       }
+      YPg[new_slot] = X(2 * no, 1);
+      ypy(new_slot, new_slot) = X(2 * no, 4);
       if (!(sy(new_slot, new_slot) > 0)) ring.clear();   // curvature lost to rounding: restart
       new_slot = -1;
     }
     const int kk = ring.count;
-    std::vector<double> Sg(kk), Yg(kk);
-    for (int i = 0; i < kk; ++i) { Sg[i] = Sgv[ring.slot(i)]; Yg[i] = Ygv[ring.slot(i)]; }
-    // --- two-loop recursion carried out on the Gram scalars
+    // --- two-loop recursion on the Gram scalars with H0 = gamma P (P the
+    // kinetic preconditioner):  q = g - sum alpha_j y_j,  r = gamma P q +
+    // sum (alpha_j - beta_j) s_j,  d = -r, where P q = P g - sum alpha_k P y_k
+    // is a combination of stored vectors and <y_i, P q> follows from the
+    // scalars <y_i, P g> and <y_i, P y_k>.
     std::vector<double> alpha(kk, 0.0), beta(kk, 0.0), rho(kk, 0.0);
     for (int i = 0; i < kk; ++i) rho[i] = 1.0 / sy(ring.slot(i), ring.slot(i));
     for (int i = kk - 1; i >= 0; --i) {
-      double sq = Sg[i];
+      double sq = Sgv[ring.slot(i)];
       for (int j = i + 1; j < kk; ++j) sq -= alpha[j] * sy(ring.slot(i), ring.slot(j));
       alpha[i] = rho[i] * sq;
     }
@@ -885,37 +909,24 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       const int sl = ring.slot(kk - 1);
       gamma = sy(sl, sl) / yy(sl, sl);
     }
-    // With the initial inverse Hessian H0 = gamma P (P the kinetic
-    // preconditioner), the middle of the two-loop recursion is r = gamma P q,
-    // q = g - sum alpha_j y_j: one linear combination, one preconditioning
-    // pass and the dots <y_i, P q> replace the scalar-only middle step.
+    for (int i = 0; i < kk; ++i) {
+      double ypq = YPg[ring.slot(i)];
+      for (int k = 0; k < kk; ++k) ypq -= alpha[k] * ypy(ring.slot(i), ring.slot(k));
+      double yr = gamma * ypq;
+      for (int j = 0; j < i; ++j) yr += (alpha[j] - beta[j]) * sy(ring.slot(j), ring.slot(i));
+      beta[i] = rho[i] * yr;
+    }
     double dd = 0, dg = 0, dpsi = 0;
     auto direction = [&](int nk) -> int {
-      int e;
-      if (nk > 0) {
-        VecList<T> ql{};
-        ql.nv = 0;
-        ql.v[ql.nv] = g; ql.c[ql.nv++] = 1.0;
-        for (int j = 0; j < nk; ++j) { ql.v[ql.nv] = Yh[ring.slot(j)]; ql.c[ql.nv++] = -alpha[j]; }
-        if ((e = lincomb(ql, qv, nullptr, nullptr, nullptr, st))) return e;
-        if ((e = precondition(qv, rv, st))) return e;
-        std::vector<const T*> Yl;
-        for (int j = 0; j < nk; ++j) Yl.push_back(Yh[ring.slot(j)]);
-        std::vector<double> yr0;
-        if ((e = gram(Yl, {rv}, yr0, st))) return e;
-        for (int i = 0; i < nk; ++i) {
-          double yr = gamma * yr0[i];
-          for (int j = 0; j < i; ++j) yr += (alpha[j] - beta[j]) * sy(ring.slot(j), ring.slot(i));
-          beta[i] = rho[i] * yr;
-        }
-      } else {
-        if ((e = precondition(g, rv, st))) return e;
-      }
-      // d = -gamma P q - sum (alpha_j - beta_j) s_j
+      // d = -gamma P g + gamma sum alpha_k P y_k - sum (alpha_j - beta_j) s_j
       VecList<T> vl{};
       vl.nv = 0;
-      vl.v[vl.nv] = rv; vl.c[vl.nv++] = nk > 0 ? -gamma : -1.0;
-      for (int j = 0; j < nk; ++j) { vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]); }
+      vl.v[vl.nv] = pgv[pcur]; vl.c[vl.nv++] = nk > 0 ? -gamma : -1.0;
+      for (int j = 0; j < nk; ++j) {
+        vl.v[vl.nv] = PYh[ring.slot(j)]; vl.c[vl.nv++] = gamma * alpha[j];
+        vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]);
+      }
+      int e;
       if ((e = lincomb(vl, d, &dd, &dg, &dpsi, st))) return e;
       if (nk == 0) t0 = 0.1 * std::sqrt(Qcur / std::max(dd, 1e-300));   // first step: 10% of |psi|
       return OFDFT_OK;

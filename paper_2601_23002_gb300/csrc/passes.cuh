@@ -520,6 +520,10 @@ template <typename T> struct EpiArgs {
   typename TreeVal<T>::type* partials;   // [gridDim.x][8], tree form (see GArgs)
   FinArgs<T> fin;        // final reduction, done by the last block to finish
   unsigned int* counter;
+  // mode 3 only: with pyout non-null, also pyout = out - pold (the minimiser's
+  // P y = P g_new - P g_old)
+  const T* pold;
+  T* pyout;
 };
 
 // smem: stg[nact][R][nh] (complex; field f's real rows overwrite its own
@@ -602,7 +606,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
   if (a.mode == 3) {
     // every block takes this branch: no partial sums, no final reduction
     const T* fP = realf[2];
-    for (int q = threadIdx.x; q < tot; q += blockDim.x) a.out[off + q] = fP[q];
+    for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+      const T v = fP[q];
+      a.out[off + q] = v;
+      if (a.pyout) a.pyout[off + q] = v - a.pold[off + q];
+    }
     return;
   }
   const bool has_n = sp.s[0] != nullptr, has_na = sp.s[1] != nullptr, has_psi = sp.s[2] != nullptr;

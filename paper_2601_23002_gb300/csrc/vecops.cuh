@@ -6,7 +6,7 @@
 namespace ofdft {
 
 constexpr int kMaxV = 16;   // vectors per gram launch (longer lists are chunked)
-constexpr int kMaxW = 4;    // targets per gram launch
+constexpr int kMaxW = 5;    // targets per gram launch
 constexpr int kMaxLin = 20; // vectors of one streamed list: a combination's 1 + 2 m <= 17 terms and its
                             // two dot targets, or kMaxV Gram vectors and kMaxW targets
 
