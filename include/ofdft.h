@@ -190,6 +190,26 @@ int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_
                      double* s_out, void* stream);
 
 /*
+ * Hellmann-Feynman forces on the ions at density rho (Methods: the molecular
+ * dynamics that produces the structure factors moves the ions with these
+ * forces).  At fixed n only the electron-ion energy E_loc and the ion-ion
+ * Ewald energy depend on the positions, so
+ *   F_I = -dE_loc/dR_I - dE_ion/dR_I
+ *       = -Z_I sum_{G != 0} G Im[ conj(v~(G) n~(G) + (4 pi/Omega) exp(-G^2/4eta^2)/G^2 S_Z(G))
+ *                                  exp(-i G.R_I) ]  +  (Ewald real-space pair forces),
+ * v~ the Gaussian-smoothed Coulomb form factor per unit charge, S_Z the
+ * charge-weighted structure factor, over the same G and with the same Ewald
+ * splitting as the energy of ofdft_energy_potential, so F is the exact
+ * derivative of that energy at fixed rho (and, at the minimum density, the
+ * total force).  The local term drops out when OFDFT_TERM_LOC is off.
+ * rho: device real field (plan precision).  forces_out: host double[n_ion * 3]
+ * (hartree/bohr), ion-major.  Requires ofdft_structure_factor first (the
+ * positions are those of the last call).  The first call builds and keeps a G
+ * list on the device.  Synchronises `stream`.
+ */
+int ofdft_forces(ofdft_plan* plan, const void* rho, double* forces_out, void* stream);
+
+/*
  * Batched form: minimise `count` independent snapshots (one plan each, any mix
  * of grid sizes and precisions) concurrently.  `concurrency` host workers
  * (>= 1) each own a CUDA stream on the plans' device and take the next plan,

@@ -144,6 +144,14 @@ class Plan:
                                          _stream_ptr(self.stream)))
         return q, s
 
+    def forces(self, rho: torch.Tensor) -> np.ndarray:
+        """Hellmann-Feynman forces [n_ion, 3] (hartree/bohr) at density rho for
+        the positions of the last set_ions (ofdft_forces)."""
+        f = np.zeros((self._Z.size, 3))
+        _check(self.lib.ofdft_forces(self._p, self._field(rho, "rho"), f.ctypes.data_as(C.c_double_p),
+                                     _stream_ptr(self.stream)))
+        return f
+
 
 def minimize_batch(plans, rhos, concurrency: int = 8, start_uniform: bool = True, tol_F_per_ion: float = 1e-6,
                    tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000, c1: float = 1e-4,

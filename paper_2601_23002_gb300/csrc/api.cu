@@ -180,6 +180,11 @@ int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_
   return plan->eng->sei_shells(rho, n_shells, q_out, s_out, stream);
 }
 
+int ofdft_forces(ofdft_plan* plan, const void* rho, double* forces_out, void* stream) {
+  if (!plan || !rho || !forces_out) { set_error("NULL argument"); return OFDFT_ERR_INVALID; }
+  return plan->eng->forces(rho, forces_out, stream);
+}
+
 int ofdft_profile_enable(ofdft_plan* plan, int timing) {
   if (!plan) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
   return plan->eng->profile_enable(timing);

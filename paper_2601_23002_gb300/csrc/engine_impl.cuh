@@ -117,6 +117,17 @@ class Engine : public IEngine {
   double E_ion = 0;
   bool ions_set = false;
   double g2cut_loc = 0;
+  // Ewald splitting of the last set_ions, reused by forces
+  double ew_eta = 0, ew_rcut = 0;
+  int ew_nimg = 0;
+  // forces: G list {kx, ky, kz, w} with 0 < |G|^2 <= g2cut_loc, its (vfac, efac),
+  // per-G weights qq, ion phases in T, device output; built on the first call
+  int4* f_gl = nullptr;
+  double2* f_gf = nullptr;
+  C* f_qq = nullptr;
+  C* f_pt = nullptr;
+  double* f_out = nullptr;
+  int f_ng = -1;
   size_t n_vloc = 0;         // half-spectrum entries with |G|^2 <= g2cut_loc
   double mean_params[4] = {0, 0, 0, 0};
   Profiler prof;
@@ -529,6 +540,7 @@ class Engine : public IEngine {
     if ((rc = sum_partials(nrows, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
     const int nimg = (int)std::ceil(rcut / L) + 1;
+    ew_eta = eta; ew_rcut = rcut; ew_nimg = nimg;
     const long ncomb = (long)nion * nion * (2 * nimg + 1) * (2 * nimg + 1) * (2 * nimg + 1);
     const int gb = (int)std::min<long>(std::min<long>(2048, 4L * nsm), (ncomb + 255) / 256);
     OFDFT_RUN("k_ewald_real", st, (double)nion * 32, k_ewald_real<<<gb, 256, 0, st>>>(pos_d, Z_d, nion, L, eta, rcut, nimg, partials));
@@ -728,6 +740,7 @@ class Engine : public IEngine {
   int minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o, ofdft_result* r, void* stream_) override;
 
   int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream_) override;
+  int forces(const void* rho, double* f_out_h, void* stream_) override;
 };
 
 // ---------------------------------------------------------------------------
@@ -1089,6 +1102,68 @@ int Engine<T>::sei_shells(const void* rho, int n_shells, double* q_out, double* 
     q_out[i] = 2.0 * kPi / L * std::sqrt((double)shell_m2[i]);
     s_out[i] = hout[2 * i] / hout[2 * i + 1];
   }
+  return OFDFT_OK;
+}
+
+// Hellmann-Feynman forces on the ions at density rho (Methods: the forces that
+// drive the molecular dynamics; at fixed n only E_loc and the Ewald energy
+// depend on the ion positions).  f_out_h: host double[n_ion * 3].
+template <typename T>
+int Engine<T>::forces(const void* rho, double* f_out_h, void* stream_) {
+  if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_forces"); return OFDFT_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream_;
+  const int nion = (int)cs.Z.size();
+  const double tp = 2.0 * kPi / L;
+  int rc;
+  if (f_ng < 0) {
+    // the G list of the local and reciprocal Ewald sums (independent of the ions)
+    std::vector<int4> gl;
+    std::vector<double2> gf;
+    const int r = (int)std::ceil(std::sqrt(g2cut_loc) / tp);
+    const bool loc = (cs.terms & OFDFT_TERM_LOC) != 0;
+    for (int mx = std::max(-h, -r); mx <= std::min(h - 1, r); ++mx)
+      for (int my = std::max(-h, -r); my <= std::min(h - 1, r); ++my)
+        for (int kz = 0; kz <= std::min(h, r); ++kz) {
+          const int m2 = mx * mx + my * my + kz * kz;
+          const double G2 = tp * tp * (double)m2;
+          if (m2 == 0 || G2 > g2cut_loc) continue;
+          const int kx = mx < 0 ? mx + n : mx, ky = my < 0 ? my + n : my;
+          const int w = (kz == 0 || 2 * kz == n) ? 1 : 2;
+          gl.push_back(make_int4(kx, ky, kz, w));
+          const double vfac = loc ? -4.0 * kPi * std::exp(-G2 * cs.rc * cs.rc / 4.0) / G2 : 0.0;
+          const double efac = 4.0 * kPi / Omega * std::exp(-G2 / (4.0 * ew_eta * ew_eta)) / G2;
+          gf.push_back(make_double2(vfac, efac));
+        }
+    const size_t ng = std::max<size_t>(1, gl.size());
+    if ((rc = alloc(&f_gl, ng)) || (rc = alloc(&f_gf, ng)) || (rc = alloc(&f_qq, ng)) ||
+        (rc = alloc(&f_pt, (size_t)nion * 3 * n)) || (rc = alloc(&f_out, (size_t)nion * 3)))
+      return rc;
+    if (!gl.empty()) {
+      OFDFT_CK(cudaMemcpyAsync(f_gl, gl.data(), gl.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+      OFDFT_CK(cudaMemcpyAsync(f_gf, gf.data(), gf.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+    }
+    OFDFT_CK(cudaStreamSynchronize(st));
+    f_ng = (int)gl.size();
+  }
+  // n~ (unnormalised) into spec[0], tiled layout
+  Spectra<T> sp{};
+  sp.s[0] = spec[0]; sp.nact = 1; sp.idx[0] = 0;
+  ProArgs<T> pa{0, (const T*)rho, nullptr, nullptr, (T)0, (T)1, (T)cs.alpha};
+  OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + (double)NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+  OFDFT_RUN("k_ypass", st, 2.0 * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+  OFDFT_RUN("k_xpass", st, 2.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 1), kThreads, smem_xp, st>>>(sp, pn, tw_n, n, xJ));
+  const int tot = nion * 3 * n;
+  OFDFT_RUN("k_phases_t", st, (double)tot * (16 + sizeof(C)), k_phases_t<T><<<std::min(4096, (tot + 255) / 256), 256, 0, st>>>(phases, f_pt, tot));
+  if (f_ng > 0) {
+    const int gq = std::min(4 * nsm, (f_ng + 127) / 128);
+    OFDFT_RUN("k_forces_q", st, (double)f_ng * (sizeof(C) + 32 + sizeof(C)), k_forces_q<T><<<gq, 128, 0, st>>>(spec[0], f_gl, f_gf, f_ng, phases, Z_d, nion, n, 1.0 / (double)N, f_qq));
+    OFDFT_RUN("k_forces_g", st, (double)nion * f_ng * (sizeof(C) + 16), k_forces_g<T><<<nion, 256, 0, st>>>(f_qq, f_gl, f_ng, f_pt, Z_d, n, tp, f_out));
+  } else {
+    OFDFT_CK(cudaMemsetAsync(f_out, 0, (size_t)nion * 3 * sizeof(double), st));
+  }
+  OFDFT_RUN("k_ewald_force_real", st, (double)nion * nion * 32, k_ewald_force_real<<<nion, 256, 0, st>>>(pos_d, Z_d, nion, L, ew_eta, ew_rcut, ew_nimg, f_out));
+  OFDFT_CK(cudaMemcpyAsync(f_out_h, f_out, (size_t)nion * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
   return OFDFT_OK;
 }
 

@@ -319,3 +319,113 @@ static __global__ void k_sum_columns(const double* __restrict__ partial, int row
 }
 
 }  // namespace ofdft
+
+namespace ofdft {
+
+// ---------------------------------------------------------------------------
+// Hellmann-Feynman forces at a given density (same derivation as the energy:
+// at fixed n the ions enter only through E_loc and the Ewald energy).
+//   F_I = -Z_I sum_G Im[qq(G) e_I(G)] G  +  Ewald real-space part,
+//   e_I(G) = exp(-i G.R_I),  qq(G) = w(G) conj(vfac(G) n~(G) + efac(G) A(G)),
+//   A(G) = sum_J Z_J exp(-i G.R_J),  vfac = -4 pi exp(-G^2 rc^2/4)/G^2 (per unit Z),
+//   efac = (4 pi / Omega) exp(-G^2/(4 eta^2))/G^2,
+// over the listed G (0 < |G|^2 within the local and Ewald cutoffs, half
+// spectrum with Hermitian weight w = 2, or 1 on the kz = 0 and n/2 planes).
+// The G list and the signed m of each index are those of k_struct, so the
+// forces are the exact derivative of the energy the evaluation computes.
+
+// one thread per listed G: qq(G); FP64 (a sum over all ions per G)
+template <typename T>
+__global__ void k_forces_q(const cplx<T>* __restrict__ nt, const int4* __restrict__ gl,
+                           const double2* __restrict__ gf, int ng, const double2* __restrict__ ph,
+                           const double* __restrict__ Z, int n_ion, int n, double invN,
+                           cplx<T>* __restrict__ qq) {
+  const int nh = n / 2 + 1;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    const int4 e = gl[g];
+    const cplx<T> v = nt[((size_t)e.x * n + e.y) * nh + e.z];
+    double ar = 0, ai = 0;
+    for (int J = 0; J < n_ion; ++J) {
+      const double2 px = ph[((size_t)J * 3 + 0) * n + e.x];
+      const double2 py = ph[((size_t)J * 3 + 1) * n + e.y];
+      const double2 pz = ph[((size_t)J * 3 + 2) * n + e.z];
+      const double xr = px.x * py.x - px.y * py.y, xi = px.x * py.y + px.y * py.x;
+      const double er = xr * pz.x - xi * pz.y, ei = xr * pz.y + xi * pz.x;
+      ar += Z[J] * er; ai += Z[J] * ei;
+    }
+    const double2 f = gf[g];                        // (vfac, efac)
+    const double w = (double)e.w;
+    const double qr = f.x * (double)v.x * invN + f.y * ar, qi = f.x * (double)v.y * invN + f.y * ai;
+    qq[g] = mk<T>((T)(w * qr), (T)(-w * qi));       // w conj(Q)
+  }
+}
+
+// e_I phases in the plan's precision: pt[(I*3 + d)*n + k] = ph[...]
+template <typename T>
+__global__ void k_phases_t(const double2* __restrict__ ph, cplx<T>* __restrict__ pt, int tot) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x)
+    pt[q] = mk<T>((T)ph[q].x, (T)ph[q].y);
+}
+
+// one block per ion: F_I(G part) = -Z_I tp sum_G Im[qq e_I] m(G) -> out[I*3 .. I*3+2]
+template <typename T>
+__global__ void __launch_bounds__(256) k_forces_g(const cplx<T>* __restrict__ qq, const int4* __restrict__ gl,
+                                                  int ng, const cplx<T>* __restrict__ pt,
+                                                  const double* __restrict__ Z, int n, double tp,
+                                                  double* __restrict__ out) {
+  __shared__ typename TreeVal<T>::type scr[3 * 257];
+  const int I = blockIdx.x;
+  const cplx<T>* px = pt + (size_t)I * 3 * n;
+  const cplx<T>* py = px + n;
+  const cplx<T>* pz = py + n;
+  Acc<T> acc[3];
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    const int4 e = gl[g];
+    const cplx<T> a = px[e.x], b = py[e.y], c = pz[e.z];
+    const cplx<T> ab = cmul(a, b);
+    const cplx<T> eI = cmul(ab, c);
+    const cplx<T> q = qq[g];
+    const T im = q.x * eI.y + q.y * eI.x;          // Im[q e_I]
+    const int mx = e.x <= n / 2 - 1 ? e.x : e.x - n;
+    const int my = e.y <= n / 2 - 1 ? e.y : e.y - n;
+    const int mz = e.z <= n / 2 - 1 ? e.z : e.z - n;   // the phase tables' convention
+    acc[0].add(im * (T)mx); acc[1].add(im * (T)my); acc[2].add(im * (T)mz);
+  }
+  double s[3];
+  block_sum_tree<3, T>(acc, 3, s, scr);
+  if (threadIdx.x < 3) out[(size_t)I * 3 + threadIdx.x] = -Z[I] * tp * s[threadIdx.x];
+}
+
+// one block per ion: Ewald real-space force added to out[I*3 ..]; FP64
+static __global__ void __launch_bounds__(256) k_ewald_force_real(const double* __restrict__ pos,
+                                                                 const double* __restrict__ Z, int n_ion, double L,
+                                                                 double eta, double rcut, int nimg,
+                                                                 double* __restrict__ out) {
+  __shared__ double red[3 * 32];
+  const int I = blockIdx.x;
+  const int side = 2 * nimg + 1;
+  const int nim3 = side * side * side;
+  const long tot = (long)n_ion * nim3;
+  const double rc2 = rcut * rcut;
+  const double c2 = 2.0 * eta / 1.7724538509055160273;   // 2 eta / sqrt(pi)
+  double f[3] = {0, 0, 0};
+  for (long q = threadIdx.x; q < tot; q += blockDim.x) {
+    const int J = (int)(q / nim3), im = (int)(q % nim3);
+    const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
+    const double x = pos[I * 3] - pos[J * 3] + a * L, y = pos[I * 3 + 1] - pos[J * 3 + 1] + b * L,
+                 z = pos[I * 3 + 2] - pos[J * 3 + 2] + c * L;
+    const double r2 = x * x + y * y + z * z;
+    if (r2 > 1e-24 && r2 < rc2) {
+      const double r = sqrt(r2);
+      const double s = Z[I] * Z[J] * (erfc(eta * r) / r2 + c2 * exp(-eta * eta * r2) / r) / r;
+      f[0] += s * x; f[1] += s * y; f[2] += s * z;
+    }
+  }
+  double o[3];
+  block_sum<3>(f, red, o);
+  if (threadIdx.x == 0) {
+    out[I * 3 + 0] += o[0]; out[I * 3 + 1] += o[1]; out[I * 3 + 2] += o[2];
+  }
+}
+
+}  // namespace ofdft
