@@ -20,6 +20,10 @@ the paper names, that it follows):
 * ``minimize``     L-BFGS on sqrt(n) at fixed electron number.
 * ``sei``          electron-ion static structure factor on |q| shells
                    (Methods, static structure factors).
+* ``forces``       Hellmann-Feynman forces on the ions (Methods, molecular
+                   dynamics).
+* ``pressure``     P = -dF/dOmega under a homogeneous dilation (Results,
+                   Table 1 and Fig. 3 report pressures).
 
 Parity status: every function is pinned by the tests in ``tests/test_oracle_*``
 against closed forms, library routines or brute force, except the end-to-end
