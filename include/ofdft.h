@@ -210,6 +210,25 @@ int ofdft_sei_shells(ofdft_plan* plan, const void* rho, int n_shells, double* q_
 int ofdft_forces(ofdft_plan* plan, const void* rho, double* forces_out, void* stream);
 
 /*
+ * Pressure P = -dF/dOmega at density rho (Results: Table 1 and Fig. 3 report
+ * the pressure of warm dense hydrogen), read as the derivative under a
+ * homogeneous dilation L, R_I -> lambda L, lambda R_I, n(r) -> n(r/lambda)/lambda^3
+ * at fixed T and N_e.  At the minimum density this is the derivative of the
+ * minimised free energy at fixed fractional ion coordinates (ion-ion term
+ * included; the ideal-gas pressure of moving ions is not).  Per term:
+ *   TF, xc:  (1/Omega) int (n v - f)      vW: 2 E_vW / (3 Omega)
+ *   Hartree, ion:  E / (3 Omega)
+ *   loc:  (1/3) sum_G Re[n~* V_loc] c(G), c = 1 - G^2 rc^2/2 (G != 0), 3 (G = 0)
+ *   NL:  -(1/3) sum_G |(n^a)~|^2 [(3 - 6a) K + dK/dlambda],
+ * dK/dlambda the derivative of K(|G|/lambda; nbar/lambda^3), formed from kernel
+ * tables at lambda = 1 +- 2e-3, 1 +- 1e-3 (Richardson) on the first call.
+ * rho: device real field.  p_out: host double[8] = {TF, vW, NL, Hartree, loc,
+ * xc, ion, total} in hartree/bohr^3.  Requires ofdft_structure_factor first.
+ * Synchronises `stream`.
+ */
+int ofdft_pressure(ofdft_plan* plan, const void* rho, double* p_out, void* stream);
+
+/*
  * Batched form: minimise `count` independent snapshots (one plan each, any mix
  * of grid sizes and precisions) concurrently.  `concurrency` host workers
  * (>= 1) each own a CUDA stream on the plans' device and take the next plan,

@@ -61,7 +61,8 @@ EXPORTS = ["ofdft_default_opts", "ofdft_default_min_opts", "ofdft_last_error", "
            "ofdft_plan_create", "ofdft_plan_destroy", "ofdft_plan_bytes", "ofdft_structure_factor",
            "ofdft_energy_potential", "ofdft_minimize", "ofdft_sei_shells",
            "ofdft_profile_enable", "ofdft_profile_read", "ofdft_sei_shells_static",
-           "ofdft_minimize_batch", "ofdft_autotune", "ofdft_set_tiles", "ofdft_forces"]
+           "ofdft_minimize_batch", "ofdft_autotune", "ofdft_set_tiles", "ofdft_forces",
+           "ofdft_pressure"]
 
 _lib = None
 
@@ -99,6 +100,8 @@ def load(path: str | None = None):
     L.ofdft_sei_shells.restype = ctypes.c_int
     L.ofdft_forces.argtypes = [vp, vp, c_double_p, vp]
     L.ofdft_forces.restype = ctypes.c_int
+    L.ofdft_pressure.argtypes = [vp, vp, c_double_p, vp]
+    L.ofdft_pressure.restype = ctypes.c_int
     L.ofdft_sei_shells_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_int, vp, vp, vp]
     L.ofdft_sei_shells_static.restype = ctypes.c_int

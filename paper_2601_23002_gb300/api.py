@@ -152,6 +152,16 @@ class Plan:
                                      _stream_ptr(self.stream)))
         return f
 
+    PRESSURE_TERMS = ("tf", "vw", "nl", "hartree", "loc", "xc", "ion", "total")
+
+    def pressure(self, rho: torch.Tensor) -> dict:
+        """Pressure -dF/dOmega (hartree/bohr^3) per term and total at density
+        rho (ofdft_pressure)."""
+        p = np.zeros(8)
+        _check(self.lib.ofdft_pressure(self._p, self._field(rho, "rho"), p.ctypes.data_as(C.c_double_p),
+                                       _stream_ptr(self.stream)))
+        return dict(zip(self.PRESSURE_TERMS, p.tolist()))
+
 
 def minimize_batch(plans, rhos, concurrency: int = 8, start_uniform: bool = True, tol_F_per_ion: float = 1e-6,
                    tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000, c1: float = 1e-4,

@@ -185,6 +185,11 @@ int ofdft_forces(ofdft_plan* plan, const void* rho, double* forces_out, void* st
   return plan->eng->forces(rho, forces_out, stream);
 }
 
+int ofdft_pressure(ofdft_plan* plan, const void* rho, double* p_out, void* stream) {
+  if (!plan || !rho || !p_out) { set_error("NULL argument"); return OFDFT_ERR_INVALID; }
+  return plan->eng->pressure(rho, p_out, stream);
+}
+
 int ofdft_profile_enable(ofdft_plan* plan, int timing) {
   if (!plan) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
   return plan->eng->profile_enable(timing);

@@ -29,6 +29,7 @@ class IEngine {
                        void* stream) = 0;
   virtual int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream) = 0;
   virtual int forces(const void* rho, double* f_out, void* stream) = 0;
+  virtual int pressure(const void* rho, double* p_out, void* stream) = 0;
   virtual size_t bytes() const = 0;
   virtual int autotune(void* stream, int* tile, double* us_per_eval) = 0;
   virtual int set_tiles(const int* tile) = 0;

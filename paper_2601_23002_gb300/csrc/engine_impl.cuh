@@ -128,6 +128,9 @@ class Engine : public IEngine {
   C* f_pt = nullptr;
   double* f_out = nullptr;
   int f_ng = -1;
+  // pressure: pnl(m^2) = (3 - 6a) K + dK/dlambda (FP64, built on the first call)
+  double* p_tab = nullptr;
+  bool p_ready = false;
   size_t n_vloc = 0;         // half-spectrum entries with |G|^2 <= g2cut_loc
   double mean_params[4] = {0, 0, 0, 0};
   Profiler prof;
@@ -741,6 +744,8 @@ class Engine : public IEngine {
 
   int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream_) override;
   int forces(const void* rho, double* f_out_h, void* stream_) override;
+  int pressure(const void* rho, double* p_out_h, void* stream_) override;
+  int build_pressure_table(cudaStream_t st);
 };
 
 // ---------------------------------------------------------------------------
@@ -1164,6 +1169,87 @@ int Engine<T>::forces(const void* rho, double* f_out_h, void* stream_) {
   OFDFT_RUN("k_ewald_force_real", st, (double)nion * nion * 32, k_ewald_force_real<<<nion, 256, 0, st>>>(pos_d, Z_d, nion, L, ew_eta, ew_rcut, ew_nimg, f_out));
   OFDFT_CK(cudaMemcpyAsync(f_out_h, f_out, (size_t)nion * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   OFDFT_CK(cudaStreamSynchronize(st));
+  return OFDFT_OK;
+}
+
+// pnl(m^2) = (3 - 6a) K(m^2) + dK/dlambda, dK the derivative of the kernel
+// K(|G|/lambda; nbar/lambda^3) along the dilation at lambda = 1: Richardson
+// extrapolation of central differences with steps 2e-3 and 1e-3 (the kernel is
+// a Lindhard quadrature with no closed form; error O(step^4)).
+template <typename T>
+int Engine<T>::build_pressure_table(cudaStream_t st) {
+  const int nm2 = 3 * h * h + 1;
+  int rc;
+  if (!p_tab && (rc = alloc(&p_tab, (size_t)5 * nm2 + 16))) return rc;
+  const double lam[4] = {1.002, 0.998, 1.001, 0.999};
+  double* mp = p_tab + (size_t)5 * nm2;
+  for (int i = 0; i < 4; ++i) {
+    const double nb = nbar / (lam[i] * lam[i] * lam[i]);
+    const double y = 9.8696044010893586188 * nb / (1.4142135623730950488 * std::pow(Te, 1.5));
+    OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, 32, 0, st>>>(y, Te, mp + 4 * i));
+  }
+  std::vector<double> mph(16);
+  OFDFT_CK(cudaMemcpyAsync(mph.data(), mp, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < 4; ++i) {
+    KernArgs ka{L * lam[i], nbar / (lam[i] * lam[i] * lam[i]), Te, mph[4 * i + 1], mph[4 * i + 2], cs.alpha, nm2};
+    OFDFT_RUN("k_kernel_table", st, (double)nm2 * 8, k_kernel_table<<<(nm2 + 127) / 128, 128, 0, st>>>(ka, p_tab + (size_t)i * nm2));
+  }
+  std::vector<double> tabs((size_t)4 * nm2), K0(nm2), pnl(nm2);
+  OFDFT_CK(cudaMemcpyAsync(tabs.data(), p_tab, tabs.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  OFDFT_CK(cudaMemcpyAsync(K0.data(), Kd, nm2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  for (int m = 0; m < nm2; ++m) {
+    const double c1 = (tabs[m] - tabs[(size_t)nm2 + m]) / (2.0 * 2e-3);
+    const double c2 = (tabs[(size_t)2 * nm2 + m] - tabs[(size_t)3 * nm2 + m]) / (2.0 * 1e-3);
+    pnl[m] = (3.0 - 6.0 * cs.alpha) * K0[m] + (4.0 * c2 - c1) / 3.0;
+  }
+  OFDFT_CK(cudaMemcpyAsync(p_tab + (size_t)4 * nm2, pnl.data(), nm2 * sizeof(double), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  p_ready = true;
+  return OFDFT_OK;
+}
+
+// Pressure P = -dF/dOmega under a homogeneous dilation at fixed T (Results,
+// Table 1 and Fig. 3 report pressures).  p_out_h (host double[8]):
+// TF, vW, NL, Hartree, loc, xc, ion, total.
+template <typename T>
+int Engine<T>::pressure(const void* rho, double* p_out_h, void* stream_) {
+  if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_pressure"); return OFDFT_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream_;
+  int rc;
+  // energies of the degree -2 / -1 terms from one evaluation
+  if ((rc = eval(0, (const T*)rho, nullptr, nullptr, 0.0, 1.0, 0.0, 0.0, nullptr, st, true))) return rc;
+  const double E_vW = res_h[1], E_H = res_h[3], Eion = res_h[6];
+  const bool nl = use_na();
+  if (nl && !p_ready && (rc = build_pressure_table(st))) return rc;
+  // n~ into spec[0], (n^a)~ into spec[1], tiled layout
+  Spectra<T> sp{};
+  sp.s[0] = spec[0]; sp.s[1] = spec[1]; sp.nact = 2; sp.idx[0] = 0; sp.idx[1] = 1;
+  ProArgs<T> pa{0, (const T*)rho, nullptr, nullptr, (T)0, (T)1, (T)cs.alpha};
+  OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + 2.0 * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+  OFDFT_RUN("k_ypass", st, 4.0 * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, 2), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+  OFDFT_RUN("k_xpass", st, 4.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 2), kThreads, smem_xp, st>>>(sp, pn, tw_n, n, xJ));
+  const int gb = 4 * nsm;
+  const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
+  OFDFT_RUN("k_pressure_r", st, (double)N * sizeof(T), k_pressure_r<T><<<gb, 256, 0, st>>>((const T*)rho, N, (T)cy, (T)Te, cs.terms, partials));
+  if ((rc = sum_partials(gb, 2, 0, st))) return rc;
+  const double tp = 2.0 * kPi / L;
+  const C* vl = (cs.terms & OFDFT_TERM_LOC) ? vloc : nullptr;
+  const double* pn_d = nl ? p_tab + (size_t)4 * (3 * h * h + 1) : nullptr;
+  OFDFT_RUN("k_pressure_g", st, 3.0 * NH * sizeof(C), k_pressure_g<T><<<gb, 256, 0, st>>>(spec[0], spec[1], vl, pn_d, n, tp * tp, g2cut_loc, cs.rc * cs.rc, 1.0 / (double)N, partials));
+  if ((rc = sum_partials(gb, 2, 2, st))) return rc;
+  OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  double* P = p_out_h;
+  P[0] = res_h[0] / (double)N;              // (1/Omega) dV sum n T p
+  P[1] = 2.0 * E_vW / (3.0 * Omega);
+  P[2] = -res_h[3] / 3.0;
+  P[3] = E_H / (3.0 * Omega);
+  P[4] = res_h[2] / 3.0;
+  P[5] = res_h[1] / (double)N;
+  P[6] = Eion / (3.0 * Omega);
+  P[7] = P[0] + P[1] + P[2] + P[3] + P[4] + P[5] + P[6];
   return OFDFT_OK;
 }
 

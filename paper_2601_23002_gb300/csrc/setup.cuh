@@ -429,3 +429,74 @@ static __global__ void __launch_bounds__(256) k_ewald_force_real(const double* _
 }
 
 }  // namespace ofdft
+
+namespace ofdft {
+
+// ---------------------------------------------------------------------------
+// Pressure P = -dF/dOmega under a homogeneous dilation (L, R_I -> lambda L,
+// lambda R_I; n -> n / lambda^3; fixed T).  The local functionals contribute
+// (1/Omega) int (n v - f): for TF that is n T p(y), for LDA xc n (v_xc - e_xc).
+// partial[block][2] = (sum n T p, sum n (v_xc - e_xc)) over the grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pressure_r(const T* __restrict__ rho, size_t N, T cy, T Te, int terms,
+                                                    double* __restrict__ partial) {
+  __shared__ typename TreeVal<T>::type scr[2 * 257];
+  Acc<T> acc[2];
+  const T nmin = (T)kNmin;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
+    const T nval = rho[q];
+    const T nf = fmax(nval, nmin);
+    if (terms & 1) {
+      T eta, p;
+      fd_eta_p(nf * cy, eta, p);
+      acc[0].add(nf * Te * p);
+    }
+    if (terms & 8) {
+      T exc, vxc;
+      pz81<T>(nf, exc, vxc);
+      acc[1].add(nval * (vxc - exc));
+    }
+  }
+  block_sum_tree<2, T>(acc, 2, partial + (size_t)blockIdx.x * 2, scr);
+}
+
+// G-space parts over the half spectrum (tiled layout, Hermitian weight w):
+//   partial[block][0] = sum w Re[n~* V_loc] c(G),  c = 3 at G = 0, 1 - G^2 rc^2/2 else
+//                       (entries with |G|^2 <= g2cut, as in the energy),
+//   partial[block][1] = sum w |(n^a)~|^2 pnl(m^2),  pnl = (3 - 6a) K + dK/dlambda.
+// nt, wt are unnormalised transforms (times invN).  FP64 sums.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pressure_g(const cplx<T>* __restrict__ nt, const cplx<T>* __restrict__ wt,
+                                                    const cplx<T>* __restrict__ vloc, const double* __restrict__ pnl,
+                                                    int n, double tp2, double g2cut, double rc2, double invN,
+                                                    double* __restrict__ partial) {
+  __shared__ double red[2 * 32];
+  const int nh = n / 2 + 1;
+  const size_t NH = (size_t)n * n * nh;
+  double acc[2] = {0, 0};
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < NH; q += (size_t)gridDim.x * blockDim.x) {
+    const int kz = (int)(q % nh);
+    const size_t row = q / nh;
+    const int kx = (int)(row / n), ky = (int)(row % n);
+    const int mx = kx <= n / 2 - 1 ? kx : kx - n, my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int m2 = mx * mx + my * my + kz * kz;
+    const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+    if (vloc) {
+      const double G2 = tp2 * (double)m2;
+      if (G2 <= g2cut) {
+        const cplx<T> a = nt[q], v = vloc[q];
+        const double c = m2 == 0 ? 3.0 : 1.0 - 0.5 * G2 * rc2;
+        acc[0] += w * c * invN * ((double)a.x * (double)v.x + (double)a.y * (double)v.y);
+      }
+    }
+    if (pnl) {
+      const cplx<T> b = wt[q];
+      acc[1] += w * invN * invN * ((double)b.x * (double)b.x + (double)b.y * (double)b.y) * pnl[m2];
+    }
+  }
+  double o[2];
+  block_sum<2>(acc, red, o);
+  if (threadIdx.x == 0) { partial[(size_t)blockIdx.x * 2] = o[0]; partial[(size_t)blockIdx.x * 2 + 1] = o[1]; }
+}
+
+}  // namespace ofdft
