@@ -1,4 +1,4 @@
-"""Electron-ion static structure factor on |q| shells for one snapshot.
+"""Electron-ion and ion-ion static structure factors on |q| shells.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -33,3 +33,21 @@ def sei_shells(rho: np.ndarray, pos: np.ndarray, L: float, n_electrons: float, n
     q = 2.0 * math.pi / L * np.sqrt(values.astype(float))
     s = np.array([prod[m2 == v].mean() for v in values]) / math.sqrt(n_electrons * len(pos))
     return q, s
+
+
+def sii_shells(pos: np.ndarray, L: float, n: int, n_shells: int = 200):
+    """Ion-ion static structure factor on the same shells:
+    S_ii(q_k) = (1/N_i) * mean over {G : |m|^2 = m2_k} of |S(G)|^2 (Methods,
+    S_ab with a = b = i, one snapshot)."""
+    ni = structure_factor(pos, n, L)
+    m2 = m2_grid(n)
+    values = np.unique(m2[m2 > 0])[:n_shells]
+    q = 2.0 * math.pi / L * np.sqrt(values.astype(float))
+    p2 = np.abs(ni) ** 2
+    s = np.array([p2[m2 == v].mean() for v in values]) / len(pos)
+    return q, s
+
+
+def trajectory_average(per_step: list) -> np.ndarray:
+    """Mean over MD steps of per-snapshot shell values (the <...> of S_ab)."""
+    return np.mean(np.asarray(per_step, dtype=float), axis=0)

@@ -91,3 +91,34 @@ def test_sei_of_gaussian_density_closed_form():
     vals = np.unique(m2[m2 > 0])[:30]
     ref = np.array([ref_grid[m2 == v].mean() for v in vals])
     assert np.allclose(got, ref, atol=1e-9)
+
+
+def test_sii_single_ion_is_one():
+    from oracle.sei import sii_shells
+    q, s = sii_shells(np.array([[0.3, 1.7, 2.2]]), 5.0, 16, 40)
+    assert np.allclose(s, 1.0, rtol=0, atol=1e-13)
+
+
+def test_sii_simple_cubic_lattice_counts_reciprocal_vectors():
+    # M^3 ions on a simple cubic lattice in the cell: S(G) = N_i when every
+    # component of m is a multiple of M, else 0, so S_ii(shell) = N_i x (share
+    # of the shell's grid vectors that are multiples of M), counted by brute force
+    from oracle.sei import sii_shells
+    M, n, L = 3, 18, 7.0
+    g = np.arange(M) * L / M
+    pos = np.array([[x, y, z] for x in g for y in g for z in g]) + 0.4
+    q, s = sii_shells(pos, L, n, 60)
+    ms = [m if m < n // 2 else m - n for m in range(n)]
+    count, hit = {}, {}
+    for a in ms:
+        for b in ms:
+            for c in ms:
+                k = a * a + b * b + c * c
+                if k == 0:
+                    continue
+                count[k] = count.get(k, 0) + 1
+                hit[k] = hit.get(k, 0) + (a % M == 0 and b % M == 0 and c % M == 0)
+    keys = sorted(count)[:60]
+    ref = np.array([M ** 3 * hit[k] / count[k] for k in keys])
+    assert np.allclose(q, 2 * math.pi / L * np.sqrt(keys), rtol=1e-15)
+    assert np.allclose(s, ref, atol=1e-10)
