@@ -98,7 +98,7 @@ typedef struct {
 typedef struct {
     double tol_F_per_ion; /* |dF|/N_ion below this for 3 consecutive iterations ...   */
     double tol_residual;  /* ... and residual below this, Ha                           */
-    int m;                /* L-BFGS memory (1..16)                                     */
+    int m;                /* L-BFGS memory (1..8)                                      */
     int max_iter;         /* iteration cap                                             */
     double c1, c2;        /* Wolfe constants (sufficient decrease, curvature)          */
 } ofdft_min_opts;
@@ -227,6 +227,58 @@ int ofdft_forces(ofdft_plan* plan, const void* rho, double* forces_out, void* st
  * Synchronises `stream`.
  */
 int ofdft_pressure(ofdft_plan* plan, const void* rho, double* p_out, void* stream);
+
+/* Ion dynamics (Methods, molecular dynamics). */
+typedef struct {
+    double dt;            /* time step, hbar/E_h (> 0)                                  */
+    double T_ion;         /* Nose-Hoover temperature, Ha; <= 0 runs NVE                 */
+    double tau;           /* thermostat period, hbar/E_h (> 0 with a thermostat);
+                             thermostat mass Q = g T_ion tau^2, g = 3 N_i - 3           */
+    int n_shells;         /* > 0: add S_ei and S_ii on that many |q| shells every step */
+    ofdft_min_opts min;   /* electronic minimisation at every step                      */
+} ofdft_md_opts;
+
+typedef struct {
+    double xi;            /* Nose-Hoover friction, 1/(hbar/E_h); carried between calls */
+    double s;             /* its time integral (enters the conserved quantity)         */
+    int steps_done;       /* out: steps completed by the last call                     */
+} ofdft_md_thermostat;
+
+typedef struct {
+    double e_pot;         /* minimised free energy at the step's positions, Ha          */
+    double kinetic;       /* ion kinetic energy, Ha                                      */
+    double conserved;     /* e_pot + kinetic, + Q xi^2/2 + g T_ion s with a thermostat  */
+    double xi;
+    int evaluations;      /* functional evaluations of the step's minimisation          */
+    int iterations;
+} ofdft_md_frame;
+
+/*
+ * Born-Oppenheimer molecular dynamics of the ions (Methods: NVT with a
+ * Nose-Hoover thermostat; the integrator is not printed).  Velocity Verlet
+ * with one Nose-Hoover variable in the symmetric Trotter splitting
+ *   NH(dt/2), v += dt F/(2m), x += dt v, [electrons], v += dt F/(2m), NH(dt/2),
+ *   NH(h): xi += h (2K - g T)/(2Q); v *= exp(-xi h); s += xi h; xi += h (2K - g T)/(2Q),
+ * time reversible, conserving frames[].conserved to O(dt^2).  At every step
+ * the electrons are minimised (o->min) at the new positions starting from the
+ * previous step's density, and the forces are those of ofdft_forces.  The
+ * first call minimises at the initial positions (from the uniform density when
+ * start_uniform != 0, else from rho_io).
+ * rho_io: device density (plan precision), in/out.  pos_io, vel_io: host
+ * double[n_ion * 3] (bohr, bohr/(hbar/E_h)); positions are kept in [0, L).
+ * mass: host double[n_ion] (electron masses).  th_io: thermostat state, in/out.
+ * frames: host [n_steps] or NULL.  With o->n_shells > 0, q_out (host
+ * [n_shells], 1/bohr) receives the shells and the step's S_ei (as
+ * ofdft_sei_shells) and S_ii(q) = <|S(G)|^2>_shell / N_i are ADDED to
+ * sei_sum, sii_sum (host [n_shells]): the caller divides by the steps to get
+ * the trajectory averages of S_ab (Methods).  On an error (e.g. a step whose
+ * minimisation does not converge: OFDFT_ERR_NOT_CONVERGED) pos_io, vel_io and
+ * th_io hold the last completed step and th_io->steps_done counts the steps.
+ * Synchronises `stream`.
+ */
+int ofdft_md_run(ofdft_plan* plan, void* rho_io, int start_uniform, double* pos_io, double* vel_io,
+                 const double* mass, const ofdft_md_opts* o, ofdft_md_thermostat* th_io, int n_steps,
+                 ofdft_md_frame* frames, double* q_out, double* sei_sum, double* sii_sum, void* stream);
 
 /*
  * Batched form: minimise `count` independent snapshots (one plan each, any mix

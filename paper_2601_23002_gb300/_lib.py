@@ -52,6 +52,20 @@ class Result(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class MdOpts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("T_ion", ctypes.c_double), ("tau", ctypes.c_double),
+                ("n_shells", ctypes.c_int), ("min", MinOpts)]
+
+
+class MdThermostat(ctypes.Structure):
+    _fields_ = [("xi", ctypes.c_double), ("s", ctypes.c_double), ("steps_done", ctypes.c_int)]
+
+
+class MdFrame(ctypes.Structure):
+    _fields_ = [("e_pot", ctypes.c_double), ("kinetic", ctypes.c_double), ("conserved", ctypes.c_double),
+                ("xi", ctypes.c_double), ("evaluations", ctypes.c_int), ("iterations", ctypes.c_int)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double)]
@@ -62,7 +76,7 @@ EXPORTS = ["ofdft_default_opts", "ofdft_default_min_opts", "ofdft_last_error", "
            "ofdft_energy_potential", "ofdft_minimize", "ofdft_sei_shells",
            "ofdft_profile_enable", "ofdft_profile_read", "ofdft_sei_shells_static",
            "ofdft_minimize_batch", "ofdft_autotune", "ofdft_set_tiles", "ofdft_forces",
-           "ofdft_pressure"]
+           "ofdft_pressure", "ofdft_md_run"]
 
 _lib = None
 
@@ -102,6 +116,10 @@ def load(path: str | None = None):
     L.ofdft_forces.restype = ctypes.c_int
     L.ofdft_pressure.argtypes = [vp, vp, c_double_p, vp]
     L.ofdft_pressure.restype = ctypes.c_int
+    L.ofdft_md_run.argtypes = [vp, vp, ctypes.c_int, c_double_p, c_double_p, c_double_p,
+                               ctypes.POINTER(MdOpts), ctypes.POINTER(MdThermostat), ctypes.c_int,
+                               ctypes.POINTER(MdFrame), c_double_p, c_double_p, c_double_p, vp]
+    L.ofdft_md_run.restype = ctypes.c_int
     L.ofdft_sei_shells_static.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_int, vp, vp, vp]
     L.ofdft_sei_shells_static.restype = ctypes.c_int

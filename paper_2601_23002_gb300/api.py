@@ -162,6 +162,38 @@ class Plan:
                                        _stream_ptr(self.stream)))
         return dict(zip(self.PRESSURE_TERMS, p.tolist()))
 
+    def md_run(self, rho: torch.Tensor, pos, vel, mass, n_steps: int, dt: float, T_ion: float = 0.0,
+               tau: float = 0.0, thermostat=(0.0, 0.0), n_shells: int = 0, start_uniform: bool = False,
+               tol_F_per_ion: float = 1e-6, tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000,
+               c1: float = 1e-4, c2: float = 0.9) -> dict:
+        """Ion dynamics (ofdft_md_run).  pos, vel: [n_ion, 3] (bohr, atomic
+        units of velocity), mass: [n_ion] (electron masses); T_ion <= 0 runs
+        NVE.  Returns the new pos, vel and thermostat (xi, s), per-step frames
+        and, with n_shells > 0, the shells q and the per-call sums of S_ei and
+        S_ii over the steps (divide by n_steps for trajectory averages)."""
+        ni = self._Z.size
+        x = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(ni, 3)).copy()
+        v = np.ascontiguousarray(np.asarray(vel, dtype=np.float64).reshape(ni, 3)).copy()
+        ms = np.ascontiguousarray(np.asarray(mass, dtype=np.float64).reshape(ni))
+        o = C.MdOpts(float(dt), float(T_ion), float(tau), int(n_shells),
+                     C.MinOpts(tol_F_per_ion, tol_residual, m, max_iter, c1, c2))
+        th = C.MdThermostat(float(thermostat[0]), float(thermostat[1]), 0)
+        frames = (C.MdFrame * max(1, n_steps))()
+        ns = max(1, int(n_shells))
+        q, sei, sii = np.zeros(ns), np.zeros(ns), np.zeros(ns)
+        dp = lambda a: a.ctypes.data_as(C.c_double_p)
+        rc = self.lib.ofdft_md_run(self._p, self._field(rho, "rho"), int(bool(start_uniform)), dp(x), dp(v),
+                                   dp(ms), ctypes.byref(o), ctypes.byref(th), int(n_steps), frames, dp(q),
+                                   dp(sei), dp(sii), _stream_ptr(self.stream))
+        out = dict(pos=x, vel=v, thermostat=(th.xi, th.s), steps_done=th.steps_done, status=rc,
+                   frames={k: np.array([getattr(frames[i], k) for i in range(th.steps_done)])
+                           for k, _ in C.MdFrame._fields_})
+        if n_shells > 0:
+            out.update(q=q, sei_sum=sei, sii_sum=sii)
+        if rc != C.OFDFT_OK:
+            _check(rc)
+        return out
+
 
 def minimize_batch(plans, rhos, concurrency: int = 8, start_uniform: bool = True, tol_F_per_ion: float = 1e-6,
                    tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000, c1: float = 1e-4,

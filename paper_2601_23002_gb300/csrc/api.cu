@@ -190,6 +190,22 @@ int ofdft_pressure(ofdft_plan* plan, const void* rho, double* p_out, void* strea
   return plan->eng->pressure(rho, p_out, stream);
 }
 
+int ofdft_md_run(ofdft_plan* plan, void* rho_io, int start_uniform, double* pos_io, double* vel_io,
+                 const double* mass, const ofdft_md_opts* o, ofdft_md_thermostat* th_io, int n_steps,
+                 ofdft_md_frame* frames, double* q_out, double* sei_sum, double* sii_sum, void* stream) {
+  if (!plan || !rho_io || !pos_io || !vel_io || !mass || !o || !th_io) { set_error("NULL argument"); return OFDFT_ERR_INVALID; }
+  if (n_steps < 0 || !(o->dt > 0)) { set_error("ofdft_md_run: n_steps >= 0 and dt > 0 required"); return OFDFT_ERR_INVALID; }
+  if (o->n_shells > 0 && (!q_out || !sei_sum || !sii_sum)) { set_error("ofdft_md_run: shell outputs required"); return OFDFT_ERR_INVALID; }
+  const ofdft_min_opts& m = o->min;
+  if (m.m < 1 || m.m > 8 || m.max_iter < 1 || !(m.c1 > 0) || !(m.c2 > m.c1) || !(m.c2 < 1)) {
+    set_error("bad minimiser options (m in 1..8, max_iter >= 1, 0 < c1 < c2 < 1)");
+    return OFDFT_ERR_INVALID;
+  }
+  th_io->steps_done = 0;
+  return plan->eng->md_run(rho_io, start_uniform, pos_io, vel_io, mass, *o, th_io, n_steps, frames, q_out,
+                           sei_sum, sii_sum, stream);
+}
+
 int ofdft_profile_enable(ofdft_plan* plan, int timing) {
   if (!plan) { set_error("plan must not be NULL"); return OFDFT_ERR_INVALID; }
   return plan->eng->profile_enable(timing);

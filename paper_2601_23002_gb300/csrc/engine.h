@@ -30,6 +30,9 @@ class IEngine {
   virtual int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream) = 0;
   virtual int forces(const void* rho, double* f_out, void* stream) = 0;
   virtual int pressure(const void* rho, double* p_out, void* stream) = 0;
+  virtual int md_run(void* rho_io, int start_uniform, double* pos_io, double* vel_io, const double* mass,
+                     const ofdft_md_opts& o, ofdft_md_thermostat* th, int n_steps, ofdft_md_frame* frames,
+                     double* q_out, double* sei_sum, double* sii_sum, void* stream) = 0;
   virtual size_t bytes() const = 0;
   virtual int autotune(void* stream, int* tile, double* us_per_eval) = 0;
   virtual int set_tiles(const int* tile) = 0;

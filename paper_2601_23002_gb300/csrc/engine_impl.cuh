@@ -131,6 +131,22 @@ class Engine : public IEngine {
   // pressure: pnl(m^2) = (3 - 6a) K + dK/dlambda (FP64, built on the first call)
   double* p_tab = nullptr;
   bool p_ready = false;
+  // |q| shells of the structure factors: CSR lists of half-spectrum entries
+  // with Hermitian weights, kept for the last n_shells asked for
+  int sh_ns = 0;
+  long long sh_entries = 0;
+  std::vector<int> sh_m2;
+  int* sh_ptr = nullptr;
+  long long* sh_idx = nullptr;
+  float* sh_w = nullptr;
+  double* sh_out = nullptr;
+  void free_shells() {
+    if (sh_ptr) cudaFree(sh_ptr);
+    if (sh_idx) cudaFree(sh_idx);
+    if (sh_w) cudaFree(sh_w);
+    if (sh_out) cudaFree(sh_out);
+    sh_ptr = nullptr; sh_idx = nullptr; sh_w = nullptr; sh_out = nullptr; sh_ns = 0;
+  }
   size_t n_vloc = 0;         // half-spectrum entries with |G|^2 <= g2cut_loc
   double mean_params[4] = {0, 0, 0, 0};
   Profiler prof;
@@ -146,6 +162,7 @@ class Engine : public IEngine {
   }
   ~Engine() override {
     for (void* p : allocs) cudaFree(p);
+    free_shells();
     if (res_h) cudaFreeHost(res_h);
   }
   size_t bytes() const override { return nbytes; }
@@ -746,6 +763,11 @@ class Engine : public IEngine {
   int forces(const void* rho, double* f_out_h, void* stream_) override;
   int pressure(const void* rho, double* p_out_h, void* stream_) override;
   int build_pressure_table(cudaStream_t st);
+  int build_shells(int n_shells, cudaStream_t st);
+  int shell_sums(const void* rho, cudaStream_t st, std::vector<double>& hout);
+  int md_run(void* rho_io, int start_uniform, double* pos_io, double* vel_io, const double* mass,
+             const ofdft_md_opts& o, ofdft_md_thermostat* th, int n_steps, ofdft_md_frame* frames,
+             double* q_out, double* sei_sum, double* sii_sum, void* stream_) override;
 };
 
 // ---------------------------------------------------------------------------
@@ -1030,11 +1052,11 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
 // ---------------------------------------------------------------------------
 // Electron-ion static structure factor on the first n_shells distinct nonzero
 // |m|^2 shells (one snapshot).
+// Shell lists for the first n_shells distinct nonzero m^2 on the grid.
 template <typename T>
-int Engine<T>::sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream_) {
-  if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_sei_shells"); return OFDFT_ERR_INVALID; }
+int Engine<T>::build_shells(int n_shells, cudaStream_t st) {
   if (n_shells < 1 || n_shells > 4096) { set_error("n_shells must be in [1, 4096]"); return OFDFT_ERR_INVALID; }
-  cudaStream_t st = (cudaStream_t)stream_;
+  if (sh_ns == n_shells) return OFDFT_OK;
   // distinct nonzero m^2 present on the grid, ascending, and their entries
   const int lim = n / 2;
   std::vector<char> present(3 * lim * lim + 1, 0);
@@ -1077,35 +1099,53 @@ int Engine<T>::sei_shells(const void* rho, int n_shells, double* q_out, double* 
     idx.insert(idx.end(), lists[i].begin(), lists[i].end());
     wts.insert(wts.end(), wl[i].begin(), wl[i].end());
   }
-  int* ptr_d = nullptr; long long* idx_d = nullptr; float* w_d = nullptr; double* out_d = nullptr;
-  OFDFT_CK(cudaMallocAsync((void**)&ptr_d, ptr.size() * sizeof(int), st));
-  OFDFT_CK(cudaMallocAsync((void**)&idx_d, std::max<size_t>(1, idx.size()) * sizeof(long long), st));
-  OFDFT_CK(cudaMallocAsync((void**)&w_d, std::max<size_t>(1, wts.size()) * sizeof(float), st));
-  OFDFT_CK(cudaMallocAsync((void**)&out_d, 2 * (size_t)ns * sizeof(double), st));
-  OFDFT_CK(cudaMemcpyAsync(ptr_d, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  OFDFT_CK(cudaMemcpyAsync(idx_d, idx.data(), idx.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
-  OFDFT_CK(cudaMemcpyAsync(w_d, wts.data(), wts.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  free_shells();
+  OFDFT_CK(cudaMalloc((void**)&sh_ptr, ptr.size() * sizeof(int)));
+  OFDFT_CK(cudaMalloc((void**)&sh_idx, std::max<size_t>(1, idx.size()) * sizeof(long long)));
+  OFDFT_CK(cudaMalloc((void**)&sh_w, std::max<size_t>(1, wts.size()) * sizeof(float)));
+  OFDFT_CK(cudaMalloc((void**)&sh_out, 3 * (size_t)ns * sizeof(double)));
+  OFDFT_CK(cudaMemcpyAsync(sh_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaMemcpyAsync(sh_idx, idx.data(), idx.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaMemcpyAsync(sh_w, wts.data(), wts.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  OFDFT_CK(cudaStreamSynchronize(st));
+  sh_m2 = shell_m2;
+  sh_ns = ns;
+  sh_entries = (long long)idx.size();
+  return OFDFT_OK;
+}
+
+// Per-shell sums at density rho for the cached shells: hout[3 s .. 3 s + 2] =
+// (sum w Re[n_e S*] / sqrt(N_e N_i), sum w |S|^2, sum w).
+template <typename T>
+int Engine<T>::shell_sums(const void* rho, cudaStream_t st, std::vector<double>& hout) {
   // forward transform of rho into spec[0]
   Spectra<T> sp{};
   sp.s[0] = spec[0]; sp.nact = 1; sp.idx[0] = 0;
   ProArgs<T> pa{0, (const T*)rho, nullptr, nullptr, (T)0, (T)1, (T)cs.alpha};
-  const int mode = 0;
-  OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
-  OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
+  OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + (double)NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+  OFDFT_RUN("k_ypass", st, 2.0 * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
   OFDFT_RUN("k_xpass", st, 2.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 1), kThreads, smem_xp, st>>>(sp, pn, tw_n, n, xJ));
   const double nion = (double)cs.Z.size();
   const double scale = Omega / (double)N / std::sqrt(Ne * nion);
-  OFDFT_RUN("k_sei_shells", st, (double)idx.size() * (2 * sizeof(C) + 12), k_sei_shells<T><<<ns, 256, 0, st>>>(spec[0], Sg, ptr_d, idx_d, w_d, scale, out_d));
-  std::vector<double> hout(2 * (size_t)ns);
-  OFDFT_CK(cudaMemcpyAsync(hout.data(), out_d, hout.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  OFDFT_CK(cudaFreeAsync(ptr_d, st));
-  OFDFT_CK(cudaFreeAsync(idx_d, st));
-  OFDFT_CK(cudaFreeAsync(w_d, st));
-  OFDFT_CK(cudaFreeAsync(out_d, st));
+  OFDFT_RUN("k_sei_shells", st, (double)sh_entries * (2 * sizeof(C) + 12), k_sei_shells<T><<<sh_ns, 256, 0, st>>>(spec[0], Sg, sh_ptr, sh_idx, sh_w, scale, sh_out));
+  hout.resize(3 * (size_t)sh_ns);
+  OFDFT_CK(cudaMemcpyAsync(hout.data(), sh_out, hout.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   OFDFT_CK(cudaStreamSynchronize(st));
-  for (int i = 0; i < ns; ++i) {
-    q_out[i] = 2.0 * kPi / L * std::sqrt((double)shell_m2[i]);
-    s_out[i] = hout[2 * i] / hout[2 * i + 1];
+  return OFDFT_OK;
+}
+
+template <typename T>
+int Engine<T>::sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream_) {
+  if (!ions_set) { set_error("ofdft_structure_factor must be called before ofdft_sei_shells"); return OFDFT_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream_;
+  int rc;
+  if ((rc = build_shells(n_shells, st))) return rc;
+  std::vector<double> hout;
+  if ((rc = shell_sums(rho, st, hout))) return rc;
+  for (int i = 0; i < sh_ns; ++i) {
+    q_out[i] = 2.0 * kPi / L * std::sqrt((double)sh_m2[i]);
+    s_out[i] = hout[3 * i] / hout[3 * i + 2];
   }
   return OFDFT_OK;
 }
@@ -1250,6 +1290,94 @@ int Engine<T>::pressure(const void* rho, double* p_out_h, void* stream_) {
   P[5] = res_h[1] / (double)N;
   P[6] = Eion / (3.0 * Omega);
   P[7] = P[0] + P[1] + P[2] + P[3] + P[4] + P[5] + P[6];
+  return OFDFT_OK;
+}
+
+// Ion dynamics (Methods, molecular dynamics): velocity Verlet with one
+// Nose-Hoover variable in a symmetric Trotter splitting,
+//   NH(dt/2)  v += dt F/(2m)  x += dt v  [electrons, F]  v += dt F/(2m)  NH(dt/2),
+//   NH(h): xi += h (2K - g T)/(2Q); v *= exp(-xi h); s += xi h; xi += h (2K - g T)/(2Q),
+// g = 3 N_i - 3, Q = g T tau^2; conserved H = F_min + K + Q xi^2/2 + g T s.
+// Every step the electrons are minimised at the new positions starting from
+// the previous density (rho_io), and the Hellmann-Feynman forces follow.
+template <typename T>
+int Engine<T>::md_run(void* rho_io, int start_uniform, double* pos_io, double* vel_io, const double* mass,
+                      const ofdft_md_opts& o, ofdft_md_thermostat* th, int n_steps, ofdft_md_frame* frames,
+                      double* q_out, double* sei_sum, double* sii_sum, void* stream_) {
+  cudaStream_t st = (cudaStream_t)stream_;
+  const int ni = (int)cs.Z.size();
+  const bool thermo = o.T_ion > 0;
+  const double g = 3.0 * ni - 3.0;
+  if (thermo && (g <= 0 || !(o.tau > 0))) {
+    set_error("ofdft_md_run: a thermostat needs at least 2 ions and tau > 0");
+    return OFDFT_ERR_INVALID;
+  }
+  const double Q = thermo ? g * o.T_ion * o.tau * o.tau : 0.0;
+  int rc;
+  if (o.n_shells > 0 && (rc = build_shells(o.n_shells, st))) return rc;
+  const size_t nc = (size_t)ni * 3;
+  std::vector<double> x(pos_io, pos_io + nc), v(vel_io, vel_io + nc), F(nc), hout;
+  for (auto& c : x) c -= L * std::floor(c / L);
+  ofdft_result r{};
+  auto electrons = [&](int uniform) -> int {
+    int e;
+    if ((e = set_ions(x.data(), 0, nullptr, st))) return e;
+    if ((e = minimize(rho_io, uniform, o.min, &r, st))) return e;
+    return forces(rho_io, F.data(), st);
+  };
+  auto kinetic = [&]() {
+    double k = 0;
+    for (size_t c = 0; c < nc; ++c) k += 0.5 * mass[c / 3] * v[c] * v[c];
+    return k;
+  };
+  auto nh = [&](double h) {
+    th->xi += 0.5 * h * (2.0 * kinetic() - g * o.T_ion) / Q;
+    const double f = std::exp(-th->xi * h);
+    for (auto& c : v) c *= f;
+    th->s += th->xi * h;
+    th->xi += 0.5 * h * (2.0 * kinetic() - g * o.T_ion) / Q;
+  };
+  if ((rc = electrons(start_uniform))) return rc;
+  const double dt = o.dt;
+  for (int step = 0; step < n_steps; ++step) {
+    const std::vector<double> x0 = x, v0 = v;
+    const double xi0 = th->xi, s0 = th->s;
+    if (thermo) nh(0.5 * dt);
+    for (size_t c = 0; c < nc; ++c) v[c] += 0.5 * dt * F[c] / mass[c / 3];
+    for (size_t c = 0; c < nc; ++c) x[c] += dt * v[c];
+    for (auto& c : x) c -= L * std::floor(c / L);
+    if ((rc = electrons(0))) {
+      // leave the state of the last completed step
+      std::copy(x0.begin(), x0.end(), pos_io);
+      std::copy(v0.begin(), v0.end(), vel_io);
+      th->xi = xi0; th->s = s0; th->steps_done = step;
+      return rc;
+    }
+    for (size_t c = 0; c < nc; ++c) v[c] += 0.5 * dt * F[c] / mass[c / 3];
+    if (thermo) nh(0.5 * dt);
+    const double K = kinetic();
+    if (frames) {
+      ofdft_md_frame& fr = frames[step];
+      fr.e_pot = r.e.F_total;
+      fr.kinetic = K;
+      fr.conserved = r.e.F_total + K + (thermo ? 0.5 * Q * th->xi * th->xi + g * o.T_ion * th->s : 0.0);
+      fr.xi = th->xi;
+      fr.evaluations = r.evaluations;
+      fr.iterations = r.iterations;
+    }
+    if (o.n_shells > 0) {
+      if ((rc = shell_sums(rho_io, st, hout))) return rc;
+      for (int k = 0; k < sh_ns; ++k) {
+        sei_sum[k] += hout[3 * k] / hout[3 * k + 2];
+        sii_sum[k] += hout[3 * k + 1] / ((double)ni * hout[3 * k + 2]);
+      }
+    }
+  }
+  if (o.n_shells > 0)
+    for (int k = 0; k < sh_ns; ++k) q_out[k] = 2.0 * kPi / L * std::sqrt((double)sh_m2[k]);
+  std::copy(x.begin(), x.end(), pos_io);
+  std::copy(v.begin(), v.end(), vel_io);
+  th->steps_done = n_steps;
   return OFDFT_OK;
 }
 

@@ -290,27 +290,29 @@ static __global__ void k_mean_density(double y, double T, double* out) {
 }
 
 // ---------------------------------------------------------------------------
-// S_ei shells: block s sums w Re[n_e(G) S*(G)] over the half-spectrum entries
-// of shell s (CSR lists built on the host; w = Hermitian weight), FP64, fixed
-// order.  out[2 s] = weighted sum, out[2 s + 1] = weighted count.
+// Structure-factor shells: block s sums over the half-spectrum entries of
+// shell s (CSR lists built on the host; w = Hermitian weight), FP64, fixed
+// order.  out[3 s] = sum w Re[n~ S*] scale, out[3 s + 1] = sum w |S|^2,
+// out[3 s + 2] = sum w.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sei_shells(const cplx<T>* __restrict__ nt, const cplx<T>* __restrict__ S,
                                                     const int* __restrict__ ptr, const long long* __restrict__ idx,
                                                     const float* __restrict__ wgt, double scale,
                                                     double* __restrict__ out) {
-  __shared__ double red[2 * 32];
+  __shared__ double red[3 * 32];
   const int s = blockIdx.x;
-  double acc[2] = {0, 0};
+  double acc[3] = {0, 0, 0};
   for (int e = ptr[s] + threadIdx.x; e < ptr[s + 1]; e += blockDim.x) {
     const long long q = idx[e];
     const cplx<T> a = nt[q], b = S[q];
     const double w = (double)wgt[e];
     acc[0] += w * ((double)a.x * (double)b.x + (double)a.y * (double)b.y) * scale;
-    acc[1] += w;
+    acc[1] += w * ((double)b.x * (double)b.x + (double)b.y * (double)b.y);
+    acc[2] += w;
   }
-  double o[2];
-  block_sum<2>(acc, red, o);
-  if (threadIdx.x == 0) { out[2 * s] = o[0]; out[2 * s + 1] = o[1]; }
+  double o[3];
+  block_sum<3>(acc, red, o);
+  if (threadIdx.x == 0) { out[3 * s] = o[0]; out[3 * s + 1] = o[1]; out[3 * s + 2] = o[2]; }
 }
 
 // out[c] = sum_r partial[r * cols + c] in a fixed order; one block, cols <= blockDim.x

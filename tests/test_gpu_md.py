@@ -1,0 +1,121 @@
+"""Ion dynamics through the C-ABI (ofdft_md_run) against the oracle's
+Nose-Hoover dynamics (oracle/md.py, pinned by closed forms and conservation
+laws), and the trajectory sums of S_ei and S_ii against the oracle's shells on
+the oracle's own snapshots.
+
+Both sides minimise the electrons tightly every step (1e-11 Ha/ion, residual
+1e-8), so their forces differ by ~1e-8 Ha/bohr and a few steps of dt = 4
+(0.1 fs, the paper's step at r_s = 1) move the ions apart by < 1e-7 bohr:
+positions are compared to 1e-6 bohr, energies to 1e-8 Ha/ion."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import md as omd
+from oracle.sei import sei_shells as oracle_sei, sii_shells as oracle_sii
+from workloads import random_cell, config_cell, md_velocities, PROTON_MASS, SEED_BASE
+import paper_2601_23002_gb300 as og
+
+TIGHT = dict(tol_F_per_ion=1e-11, tol_residual=1e-8)
+
+
+def _oracle_run(cell, vel, n_steps, dt, T_ion=None, tau=None):
+    mass = np.full(cell.n_ion, PROTON_MASS)
+    st = omd.MDState(pos=np.asarray(cell.pos, float).copy(), vel=vel.copy())
+    fn = omd.ofdft_force_fn(cell, dict(tol_F=1e-11, tol_R=1e-8, max_iter=4000))
+    snaps = []
+
+    def recording(pos, payload):
+        e, f, rho = fn(pos, payload)
+        snaps.append((np.array(pos), rho))
+        return e, f, rho
+    fr = omd.run(st, mass, recording, n_steps, dt, L=cell.L, T=T_ion, tau=tau)
+    return st, fr, snaps[1:]          # snapshots after each step
+
+
+@pytest.mark.parametrize("thermostat", [False, True])
+def test_md_matches_oracle(thermostat):
+    cell = random_cell(SEED_BASE + 61, 6, 1.0, 1.7, 1.0, 24)
+    mass = np.full(cell.n_ion, PROTON_MASS)
+    T_ion = cell.T
+    vel = md_velocities(SEED_BASE + 62, mass, T_ion)
+    kw = dict(T_ion=T_ion, tau=200.0) if thermostat else {}
+    n_steps, dt, ns = 4, 4.0, 40
+    st, fr, snaps = _oracle_run(cell, vel, n_steps, dt, kw.get("T_ion"), kw.get("tau"))
+    plan = og.plan_for_cell(cell)
+    rho = torch.empty(cell.n ** 3, dtype=torch.float64, device="cuda")
+    out = plan.md_run(rho, cell.pos, vel, mass, n_steps, dt, start_uniform=True, n_shells=ns,
+                      thermostat=(0.0, 0.0), **kw, **TIGHT)
+    plan.close()
+    assert out["steps_done"] == n_steps
+    ni = cell.n_ion
+    print("pos err", np.abs(out["pos"] - st.pos).max(), "vel err", np.abs(out["vel"] - st.vel).max())
+    assert np.abs(out["pos"] - st.pos).max() < 1e-6
+    assert np.abs(out["vel"] - st.vel).max() < 1e-6 * np.abs(st.vel).max()
+    for k, ref in (("e_pot", [f.e_pot for f in fr]), ("kinetic", [f.kinetic for f in fr]),
+                   ("conserved", [f.conserved for f in fr])):
+        assert np.abs(out["frames"][k] - np.array(ref)).max() < 1e-8 * ni, k
+    if thermostat:
+        assert abs(out["thermostat"][0] - st.xi) < 1e-8 * max(1e-6, abs(st.xi))
+    # trajectory sums of the structure factors on the oracle's snapshots
+    sei = sum(oracle_sei(r, p, cell.L, cell.n_electrons, ns)[1] for p, r in snaps)
+    sii = sum(oracle_sii(p, cell.L, cell.n, ns)[1] for p, r in snaps)
+    q = oracle_sei(snaps[0][1], snaps[0][0], cell.L, cell.n_electrons, ns)[0]
+    assert np.allclose(out["q"], q, rtol=1e-14)
+    assert np.abs(out["sei_sum"] - sei).max() < 1e-6
+    assert np.abs(out["sii_sum"] - sii).max() < 1e-6
+
+
+def test_md_continues_across_calls():
+    # two calls of 2 steps = one call of 4 steps (the thermostat state carries)
+    cell = random_cell(SEED_BASE + 63, 5, 1.0, 1.8, 1.0, 24)
+    mass = np.full(cell.n_ion, PROTON_MASS)
+    vel = md_velocities(SEED_BASE + 64, mass, cell.T)
+    kw = dict(dt=4.0, T_ion=cell.T, tau=150.0, **TIGHT)
+    plan = og.plan_for_cell(cell)
+    r1 = torch.empty(cell.n ** 3, dtype=torch.float64, device="cuda")
+    a = plan.md_run(r1, cell.pos, vel, mass, 4, start_uniform=True, **kw)
+    r2 = torch.empty_like(r1)
+    b = plan.md_run(r2, cell.pos, vel, mass, 2, start_uniform=True, **kw)
+    b = plan.md_run(r2, b["pos"], b["vel"], mass, 2, thermostat=b["thermostat"], **kw)
+    plan.close()
+    assert np.abs(a["pos"] - b["pos"]).max() < 1e-7
+    assert abs(a["frames"]["conserved"][-1] - b["frames"]["conserved"][-1]) < 1e-7
+
+
+def test_md_reports_a_failed_step():
+    cell = random_cell(SEED_BASE + 65, 4, 1.0, 1.8, 1.0, 16)
+    mass = np.full(cell.n_ion, PROTON_MASS)
+    plan = og.plan_for_cell(cell)
+    rho = torch.empty(cell.n ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(og.OfdftError):
+        plan.md_run(rho, cell.pos, np.zeros((4, 3)), mass, 3, 4.0, start_uniform=True, max_iter=1)
+    with pytest.raises(og.OfdftError):
+        plan.md_run(rho, cell.pos, np.zeros((4, 3)), mass, 3, -1.0, start_uniform=True)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_128_nve_conserves_energy(precision):
+    # 64 H at r_s = 2 on 128^3: 12 NVE steps of 0.1 fs; the conserved energy
+    # stays within a few per cent of the kinetic energy's swing (O(dt^2)
+    # integrator error, ~1.5% at this step on a smaller cell, plus the
+    # minimiser's tolerance)
+    cell = config_cell(2)
+    mass = np.full(cell.n_ion, PROTON_MASS)
+    vel = md_velocities(SEED_BASE + 66, mass, cell.T)
+    plan = og.plan_for_cell(cell, precision=precision)
+    dt_ = torch.float32 if precision == "fp32" else torch.float64
+    rho = torch.empty(cell.n ** 3, dtype=dt_, device="cuda")
+    tol = dict(tol_F_per_ion=1e-9, tol_residual=1e-6) if precision == "fp64" else {}
+    out = plan.md_run(rho, cell.pos, vel, mass, 12, 4.0, start_uniform=True, **tol)
+    plan.close()
+    f = out["frames"]
+    H, K = f["conserved"], f["kinetic"]
+    swing = K.max() - K.min()
+    print(precision, "H drift", np.abs(H - H[0]).max(), "K swing", swing, "evals/step", f["evaluations"])
+    assert np.abs(H - H[0]).max() < 0.05 * swing + 64 * 1e-6
+    assert f["evaluations"].max() < 60

@@ -175,3 +175,31 @@ def serving_requests(count: int = 2000, spacing: float = 0.25, lo: int = 32,
         cells.append(Cell(L=L, n=n, Z=np.full(n_ion, Z), pos=pos, theta=theta,
                           label=f"r{i}_N{n_ion}_Z{Z:g}_n{n}", meta={"rs": rs}))
     return arrivals, cells
+
+
+PROTON_MASS = 1836.15267343          # electron masses (CODATA 2018)
+BOHR_PER_ANGSTROM = 1.0 / 0.529177210903
+
+
+def md_velocities(seed: int, mass, T_ion: float) -> np.ndarray:
+    """Seeded Maxwell-Boltzmann velocities [n_ion, 3] at temperature T_ion
+    (Ha, atomic units), with the total momentum removed."""
+    mass = np.asarray(mass, dtype=float)
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(len(mass), 3)) * np.sqrt(T_ion / mass)[:, None]
+    p = (mass[:, None] * v).sum(axis=0)
+    return v - p / mass.sum()
+
+
+def hydrogen_md_cells() -> list[Cell]:
+    """The three warm-dense-hydrogen MD systems whose time per MD step the
+    paper tabulates (Methods, Table 2): 32 H at r_s = 1, 14 H at r_s = 2 and
+    14 H at r_s = 3.23, all at theta = 1, on a 0.10 Angstrom grid (rounded up
+    to an even 2,3,5-smooth size), seeded random liquid-like positions."""
+    out = []
+    for i, (n_ion, rs) in enumerate(((32, 1.0), (14, 2.0), (14, 3.23))):
+        L = (n_ion * 4.0 * math.pi * rs ** 3 / 3.0) ** (1.0 / 3.0)
+        n = smooth_grid(L, 0.10 * BOHR_PER_ANGSTROM, 8, 512)
+        out.append(random_cell(SEED_BASE + 5000 + i, n_ion, 1.0, rs, 1.0, n, min_sep=0.6 * rs,
+                               label=f"md_H{n_ion}_rs{rs:g}_n{n}"))
+    return out
