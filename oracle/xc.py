@@ -12,6 +12,16 @@ parametrisation of the Ceperley-Alder correlation energy:
   e_c = gamma / (1 + beta1 sqrt(r_s) + beta2 r_s)           (r_s >= 1)
   e_c = A ln r_s + B + C r_s ln r_s + D r_s                 (r_s <  1)
   v_c = e_c - (r_s / 3) d e_c / d r_s
+
+PZ81 fixes B and D of the high-density branch by requiring e_c and
+d e_c / d r_s to be continuous at r_s = 1, where the two branches meet.  The
+published three-digit values (B = -0.048, D = -0.0116) are the rounding of
+that solution and leave a step of 3.2e-5 Ha in e_c (2.8e-5 Ha in v_c) at
+r_s = 1, which no minimiser can settle across: a density that straddles
+r_s = 1 (hydrogen at r_s = 1) stalls with its residual stuck near 3e-4 Ha.
+Reading used here: B and D are solved from the two continuity conditions
+given gamma, beta1, beta2, A and C (they differ from the printed values by
+1.9e-5 and 1.3e-5).
 """
 from __future__ import annotations
 
@@ -20,7 +30,12 @@ import math
 import numpy as np
 
 GAMMA, BETA1, BETA2 = -0.1423, 1.0529, 0.3334
-A, B, C, D = 0.0311, -0.048, 0.0020, -0.0116
+A, C = 0.0311, 0.0020
+# continuity at r_s = 1:  B + D = gamma / (1 + beta1 + beta2)  and
+# A + C + D = -gamma (beta1/2 + beta2) / (1 + beta1 + beta2)^2
+_DEN1 = 1.0 + BETA1 + BETA2
+D = -GAMMA * (0.5 * BETA1 + BETA2) / _DEN1 ** 2 - A - C
+B = GAMMA / _DEN1 - D
 CX = 0.75 * (3.0 / math.pi) ** (1.0 / 3.0)
 
 

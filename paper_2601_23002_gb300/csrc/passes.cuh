@@ -115,6 +115,16 @@ static __device__ __forceinline__ void fd_eta_p(float y, float& eta, float& p) {
 }
 
 // Perdew-Zunger LDA, unpolarised: returns e_xc per electron, v_xc.
+// PZ81 joins its two correlation branches at r_s = 1 by continuity of e_c and
+// d e_c / d r_s, which fixes B and D from the other constants; the printed
+// three-digit B = -0.048, D = -0.0116 are their rounding and leave a 3.2e-5 Ha
+// step at r_s = 1 that stalls the minimiser on densities straddling it.
+constexpr double kPzG = -0.1423, kPzB1 = 1.0529, kPzB2 = 0.3334, kPzA = 0.0311, kPzC = 0.0020;
+constexpr double kPzDen1 = 1.0 + kPzB1 + kPzB2;
+// A + C + D = d e_c/d r_s of the low-density branch at 1;  B + D = its e_c at 1
+constexpr double kPzD = -kPzG * (0.5 * kPzB1 + kPzB2) / (kPzDen1 * kPzDen1) - kPzA - kPzC;
+constexpr double kPzB = kPzG / kPzDen1 - kPzD;
+
 template <typename T>
 __device__ __forceinline__ void pz81(T n, T& exc, T& vxc) {
   const T third = (T)(1.0 / 3.0);
@@ -125,13 +135,13 @@ __device__ __forceinline__ void pz81(T n, T& exc, T& vxc) {
   const T vx = (T)(4.0 / 3.0) * ex;
   T ec, vc;
   if (rs >= (T)1) {
-    const T g = (T)-0.1423, b1 = (T)1.0529, b2 = (T)0.3334;
+    const T g = (T)kPzG, b1 = (T)kPzB1, b2 = (T)kPzB2;
     const T sq = sqrt(rs);
     const T den = (T)1 + b1 * sq + b2 * rs;
     ec = g / den;
     vc = ec * ((T)1 + (T)(7.0 / 6.0) * b1 * sq + (T)(4.0 / 3.0) * b2 * rs) / den;
   } else {
-    const T A = (T)0.0311, B = (T)-0.048, C = (T)0.0020, D = (T)-0.0116;
+    const T A = (T)kPzA, B = (T)kPzB, C = (T)kPzC, D = (T)kPzD;
     const T ln = log(rs);
     ec = A * ln + B + C * rs * ln + D * rs;
     vc = A * ln + (B - A * third) + (T)(2.0 / 3.0) * C * rs * ln + ((T)2 * D - C) * third * rs;
@@ -150,13 +160,13 @@ __device__ __forceinline__ void pz81<float>(float n, float& exc, float& vxc) {
   const float vx = (4.0f / 3.0f) * ex;
   float ec, vc;
   if (rs >= 1.0f) {
-    const float g = -0.1423f, b1 = 1.0529f, b2 = 0.3334f;
+    const float g = (float)kPzG, b1 = (float)kPzB1, b2 = (float)kPzB2;
     const float sq = sqrtf(rs);
     const float inv = __fdividef(1.0f, 1.0f + b1 * sq + b2 * rs);
     ec = g * inv;
     vc = ec * (1.0f + (7.0f / 6.0f) * b1 * sq + (4.0f / 3.0f) * b2 * rs) * inv;
   } else {
-    const float A = 0.0311f, B = -0.048f, C = 0.0020f, D = -0.0116f;
+    const float A = (float)kPzA, B = (float)kPzB, C = (float)kPzC, D = (float)kPzD;
     const float ln = __logf(rs);
     ec = A * ln + B + C * rs * ln + D * rs;
     vc = A * ln + (B - A * (1.0f / 3.0f)) + (2.0f / 3.0f) * C * rs * ln + (2.0f * D - C) * (1.0f / 3.0f) * rs;

@@ -20,12 +20,16 @@ def test_exchange_closed_form():
     assert np.allclose(vx, 4 / 3 * ex, rtol=1e-15)
 
 
-def test_pz_branches_continuous_at_rs_1():
+def test_pz_branches_join_smoothly_at_rs_1():
+    # e_c and v_c (hence d e_c / d r_s) continuous at r_s = 1, and B, D the
+    # printed PZ81 values up to their last printed digit
     n1 = 3 / (4 * math.pi)
-    e_lo, _ = xc.correlation(np.array([n1 * (1 + 1e-12)]))
-    e_hi, _ = xc.correlation(np.array([n1 * (1 - 1e-12)]))
-    assert abs(e_lo[0] - e_hi[0]) < 5e-5           # PZ81 is continuous to 1e-5 Ha
+    e_lo, v_lo = xc.correlation(np.array([n1 * (1 + 1e-12)]))
+    e_hi, v_hi = xc.correlation(np.array([n1 * (1 - 1e-12)]))
+    assert abs(e_lo[0] - e_hi[0]) < 1e-13
+    assert abs(v_lo[0] - v_hi[0]) < 1e-11
     assert abs(e_hi[0] - (-0.1423 / (1 + 1.0529 + 0.3334))) < 1e-9
+    assert abs(xc.B - (-0.048)) < 5e-5 and abs(xc.D - (-0.0116)) < 5e-5
 
 
 @pytest.mark.parametrize("n0", [1e-4, 5e-3, 0.2, 3.0])
