@@ -580,12 +580,15 @@ class Engine : public IEngine {
 
   // One evaluation.  mode 0: density rho; mode 1: psi + t d with scale.
   // Leaves results in res_d[0..13]; copies them to res_h when sync != 0.
+  // dsc (device, optional): the trial's scale and psi shift as formed by
+  // k_lincomb (TrialScale); the host values scale, Q, psid are then only used
+  // when sync is set, and the caller finishes with finish_eval instead.
   int eval(int mode, const T* rho, const T* ps, const T* dd, double t, double scale, double Q, double psid,
-           T* out, cudaStream_t st, bool sync, double mu_ref = 0.0) {
+           T* out, cudaStream_t st, bool sync, double mu_ref = 0.0, const double* dsc = nullptr) {
     Spectra<T> sp = spectra();
     // psi of the uniform density: sqrt(nbar) for a given rho, sqrt(nbar / scale) for psi + t d
     const double psi_bar = std::sqrt(nbar / (mode == 0 ? 1.0 : scale));
-    ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)psi_bar};
+    ProArgs<T> pa{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)psi_bar, dsc};
     const double tp = 2.0 * kPi / L;
     using TV = typename TreeVal<T>::type;          // 8 bytes, like the double slots of partials
     TV* pt = reinterpret_cast<TV*>(partials);
@@ -611,7 +614,7 @@ class Engine : public IEngine {
     FinArgs<T> fa{pt, g_rows, pe, grid_z, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
     EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
-                  counters + 0};
+                  counters + 0, nullptr, nullptr, dsc};
     OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -735,14 +738,15 @@ class Engine : public IEngine {
 
   // out = sum_i c_i V_i; returns <out,out>, <out,g>, <out,psi> (times dV);
   // with dd == nullptr the dots are not read back (no host synchronisation)
-  int lincomb(const VecList<T>& terms, T* out, double* dd, double* dg, double* dpsi, cudaStream_t st) {
+  int lincomb(const VecList<T>& terms, T* out, double* dd, double* dg, double* dpsi, cudaStream_t st,
+              TrialScale ts = TrialScale{}) {
     VecList<T> xl = terms;
     const int nv = terms.nv;
     xl.v[nv] = g; xl.v[nv + 1] = psi;
     xl.nv = nv + 2;
     OFDFT_RUN("k_lincomb", st, (double)(nv + 3) * N * sizeof(T),
               k_lincomb<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(kMaxLin - 1), nv + 2), st>>>(
-                  xl, nv, out, N, partials, counters + 2, res_d + 16));
+                  xl, nv, out, N, partials, counters + 2, res_d + 16, ts));
     if (!dd) return OFDFT_OK;
     int rc;
     if ((rc = read_results(st))) return rc;
@@ -957,6 +961,11 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       beta[i] = rho[i] * yr;
     }
     double dd = 0, dg = 0, dpsi = 0;
+    // with history, the first trial (t = 1) is launched right behind the
+    // direction pass, its scale formed on the device (res_d[126, 127]); the
+    // host reads the direction's dots and the trial's result in one round trip
+    bool first_ready = false;
+    double first_f = 0, first_slope = 0, first_E[14], first_scale = 0, first_mu = 0;
     auto direction = [&](int nk) -> int {
       // d = -gamma P g + gamma sum alpha_k P y_k - sum (alpha_j - beta_j) s_j
       VecList<T> vl{};
@@ -967,12 +976,33 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
         vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]);
       }
       int e;
-      if ((e = lincomb(vl, d, &dd, &dg, &dpsi, st))) return e;
-      if (nk == 0) t0 = 0.1 * std::sqrt(Qcur / std::max(dd, 1e-300));   // first step: 10% of |psi|
+      if (nk == 0) {
+        if ((e = lincomb(vl, d, &dd, &dg, &dpsi, st))) return e;
+        t0 = 0.1 * std::sqrt(Qcur / std::max(dd, 1e-300));   // first step: 10% of |psi|
+        return OFDFT_OK;
+      }
+      TrialScale ts{Qcur, 1.0, Ne, dV, nbar, res_d + 126};
+      if ((e = lincomb(vl, d, nullptr, nullptr, nullptr, st, ts))) return e;
+      if ((e = eval(1, nullptr, psi, d, 1.0, 1.0, 0.0, 0.0, gp, st, false, mu_ref, res_d + 126))) return e;
+      ++evals;
+      OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaMemcpyAsync(res_h + 126, res_d + 126, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+      dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
+      t0 = 1.0;
+      const double sc = res_h[126];
+      finish_eval(1, sc, Qcur + 2.0 * dpsi + dd, dpsi + dd, mu_ref, merged());
+      first_f = res_h[13] > 0 ? NAN : res_h[7];
+      first_slope = res_h[11];
+      first_scale = sc; first_mu = res_h[9];
+      std::memcpy(first_E, res_h, sizeof(first_E));
+      first_ready = true;
       return OFDFT_OK;
     };
     if ((rc = direction(kk))) return rc;
     if (!(dg < 0) && kk > 0) {
+      first_ready = false;
       // not a descent direction: drop the history and restart along -P g
       ring.clear();
       if ((rc = direction(0))) return rc;
@@ -981,6 +1011,14 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     // --- strong-Wolfe line search along d
     double lastScale = 0, lastMu = 0, lastE[14];
     auto phi = [&](double t, double* f, double* slope) -> int {
+      if (first_ready && t == 1.0) {
+        first_ready = false;
+        *f = first_f; *slope = first_slope;
+        lastScale = first_scale; lastMu = first_mu;
+        std::memcpy(lastE, first_E, sizeof(lastE));
+        return OFDFT_OK;
+      }
+      first_ready = false;
       const double Qt = Qcur + 2.0 * t * dpsi + t * t * dd;
       const double sc = Ne / Qt;
       int e = eval(1, nullptr, psi, d, t, sc, Qt, dpsi + t * dd, gp, st, true, mu_ref);
@@ -1050,9 +1088,8 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
 
 
 // ---------------------------------------------------------------------------
-// Electron-ion static structure factor on the first n_shells distinct nonzero
-// |m|^2 shells (one snapshot).
-// Shell lists for the first n_shells distinct nonzero m^2 on the grid.
+// Structure factors on |q| shells.  Shell lists for the first n_shells
+// distinct nonzero m^2 on the grid.
 template <typename T>
 int Engine<T>::build_shells(int n_shells, cudaStream_t st) {
   if (n_shells < 1 || n_shells > 4096) { set_error("n_shells must be in [1, 4096]"); return OFDFT_ERR_INVALID; }

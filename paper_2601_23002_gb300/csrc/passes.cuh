@@ -194,6 +194,9 @@ template <typename T> struct ProArgs {
   // gradient amplifies that rounding, so in FP32 this lowers the gradient's
   // noise floor several times.
   T psi_shift;
+  // when set, scale = dsc[0] and psi_shift = dsc[1] (a trial scale formed on
+  // the device, see TrialScale)
+  const double* dsc;
 };
 
 // smem: psit[R][n] (T) | dbuf[R][n] (T) | buf0[R][P] | buf1[R][P] (complex)
@@ -228,7 +231,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
     else psit[q] = x + tstep * dbuf[q];
   }
   __syncthreads();
-  const T scale = a.scale, alpha = a.alpha, nmin = (T)kNmin;
+  const T scale = a.dsc ? (T)a.dsc[0] : a.scale, alpha = a.alpha, nmin = (T)kNmin;
+  const T psi_shift = a.dsc ? (T)a.dsc[1] : a.psi_shift;
   const unsigned Mh = qmagic(h), Mnh = qmagic(nh), MR = qmagic(R);
   const size_t nn = (size_t)n * n;
   for (int f = 0; f < sp.nact; ++f) {
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
       const int r = qdiv(q, h, Mh), k = q - r * h;
       T x0 = psit[r * n + 2 * k], x1 = psit[r * n + 2 * k + 1];
-      if (fid == 2) { x0 -= a.psi_shift; x1 -= a.psi_shift; }
+      if (fid == 2) { x0 -= psi_shift; x1 -= psi_shift; }
       if (fid == 0) {
         if (a.mode == 0) { x0 = dbuf[r * n + 2 * k]; x1 = dbuf[r * n + 2 * k + 1]; }
         else { x0 = scale * x0 * x0; x1 = scale * x1 * x1; }
@@ -534,6 +538,7 @@ template <typename T> struct EpiArgs {
   // P y = P g_new - P g_old)
   const T* pold;
   T* pyout;
+  const double* dsc;     // when set, scale = dsc[0] (a trial scale formed on the device)
 };
 
 // smem: stg[nact][R][nh] (complex; field f's real rows overwrite its own
@@ -630,7 +635,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
   const T Te = a.T_e;
   const T cy = a.cy;
   const T alpha = a.alpha, nmin = (T)kNmin;
-  const T tstep = a.t, tscale = a.scale, muref = a.mu_ref;
+  const T tstep = a.t, tscale = a.dsc ? (T)a.dsc[0] : a.scale, muref = a.mu_ref;
   AccShort<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
   const T* pd = pin + (size_t)Rfull * n;

@@ -165,12 +165,22 @@ k_gram(VecList<T> X, int nv, size_t N, double* __restrict__ partial, unsigned in
   }
 }
 
+// The scale of a line-search trial psi + t d (n = N_e (psi + t d)^2 / Q(t),
+// Q(t) = Q + 2 t <d,psi> + t^2 <d,d>) and the mean-psi shift sqrt(nbar/scale),
+// formed on the device from the direction's dots so that the first trial can
+// be launched without a host round trip.  out == nullptr: not wanted.
+struct TrialScale {
+  double q, t, ne, dv, nbar;
+  double* out;       // out[0] = scale, out[1] = sqrt(nbar / scale)
+};
+
 // out = sum_{i < nv} c_i X_i, with X_nv = A and X_{nv+1} = B; the last block
-// writes res[0..2] = <out,out>, <out,A>, <out,B>
+// writes res[0..2] = <out,out>, <out,A>, <out,B> (raw sums, without dV) and,
+// with B = psi, the trial scale of ts
 template <typename T>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k_lincomb(VecList<T> X, int nv, T* __restrict__ out, size_t N, double* __restrict__ partial,
-          unsigned int* __restrict__ counter, double* __restrict__ res) {
+          unsigned int* __restrict__ counter, double* __restrict__ res, TrialScale ts) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[32];
   using V = typename V16<T>::type;
@@ -207,6 +217,15 @@ k_lincomb(VecList<T> X, int nv, T* __restrict__ out, size_t N, double* __restric
   if (arrive_last(counter)) {
     block_sum_columns(partial, gridDim.x, 3, res, red);
     if (threadIdx.x == 0) *counter = 0u;
+    if (ts.out) {
+      __syncthreads();                   // res[] written by this block's threads
+      if (threadIdx.x == 0) {
+        const double dd = res[0] * ts.dv, dpsi = res[2] * ts.dv;
+        const double sc = ts.ne / (ts.q + 2.0 * ts.t * dpsi + ts.t * ts.t * dd);
+        ts.out[0] = sc;
+        ts.out[1] = sqrt(ts.nbar / sc);
+      }
+    }
   }
 }
 
