@@ -322,13 +322,15 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
 __device__ __forceinline__ void block_sum_columns(const double* partial, int rows, int cols, double* out,
                                                   double* /*unused*/) {
   __shared__ double colscr[1024];
-  const int k = blockDim.x / cols;
+  // k = the largest power of two with k * cols <= blockDim.x threads per column
+  int k = 1;
+  while (2 * k * cols <= (int)blockDim.x) k *= 2;
   const int t = threadIdx.x;
+  const int c = t % cols, g = t / cols;
   double v = 0;
-  if (t < k * cols) {
-    const int c = t % cols;
+  if (g < k) {
     // eight rows' loads in flight at a time, added in row order
-    int r = t / cols;
+    int r = g;
     for (; r + 7 * k < rows; r += 8 * k) {
       double x[8];
 #pragma unroll
@@ -337,14 +339,16 @@ __device__ __forceinline__ void block_sum_columns(const double* partial, int row
       for (int u = 0; u < 8; ++u) v += x[u];
     }
     for (; r < rows; r += k) v += __ldcg(partial + (size_t)r * cols + c);
+    colscr[g * cols + c] = v;
   }
-  colscr[t] = v;
   __syncthreads();
-  if (t < cols) {
-    double s2 = 0;
-    for (int g = 0; g < k; ++g) s2 += colscr[g * cols + t];
-    out[t] = s2;
+  // pairwise tree over the k group sums of each column (fixed order): log2(k)
+  // dependent FP64 additions instead of k
+  for (int h = k / 2; h >= 1; h /= 2) {
+    if (g < h) colscr[g * cols + c] += colscr[(g + h) * cols + c];
+    __syncthreads();
   }
+  if (t < cols) out[t] = colscr[t];
   __syncthreads();
 }
 

@@ -86,6 +86,7 @@ class Engine : public IEngine {
   size_t nbytes = 0;
   C *tw_n = nullptr, *tw_h = nullptr;
   double* Kd = nullptr;
+  double2* sf_tab = nullptr;   // per m^2: (v~/Omega per unit charge, Ewald reciprocal weight)
   T* Kt = nullptr;
   C* vloc = nullptr;
   C* Sg = nullptr;
@@ -396,6 +397,23 @@ class Engine : public IEngine {
     }
     g2cut_loc = 156.0 / (cs.rc * cs.rc);
     {
+      // structure-factor tables by m^2 (FP64, host): v~(G)/Omega per unit charge
+      // (-4 pi exp(-G^2 rc^2/4)/G^2, pi rc^2 at G = 0) and the Ewald reciprocal
+      // weight (2 pi/Omega) exp(-G^2/(4 eta^2))/G^2
+      const double tp2d = (2.0 * kPi / L) * (2.0 * kPi / L);
+      const double eta = ewald_eta();
+      std::vector<double2> tab(nm2);
+      for (int m2 = 0; m2 < nm2; ++m2) {
+        const double G2 = tp2d * m2;
+        if (m2 == 0) { tab[m2] = make_double2(kPi * cs.rc * cs.rc / Omega, 0.0); continue; }
+        tab[m2] = make_double2(-4.0 * kPi * std::exp(-G2 * cs.rc * cs.rc / 4.0) / G2 / Omega,
+                               2.0 * kPi / Omega * std::exp(-G2 / (4.0 * eta * eta)) / G2);
+      }
+      if ((rc = alloc(&sf_tab, nm2))) return rc;
+      OFDFT_CK(cudaMemcpyAsync(sf_tab, tab.data(), nm2 * sizeof(double2), cudaMemcpyHostToDevice, st));
+      OFDFT_CK(cudaStreamSynchronize(st));
+    }
+    {
       const double tp2 = (2.0 * kPi / L) * (2.0 * kPi / L);
       n_vloc = 0;
       for (int kx = 0; kx < n; ++kx)
@@ -410,6 +428,13 @@ class Engine : public IEngine {
   }
 
   long long grid_points() const override { return (long long)N; }
+
+  // Ewald splitting: reciprocal weights exp(-G^2/(4 eta^2)) below 1e-17 at g2max
+  double ewald_g2max() const {
+    const double gnyq = kPi * n / L;
+    return std::min(g2cut_loc, gnyq * gnyq);
+  }
+  double ewald_eta() const { return std::sqrt(ewald_g2max() / (4.0 * 39.0)); }
 
   bool tiles_fit(int r, int j) const {
     const size_t lim = 227 * 1024;
@@ -539,10 +564,8 @@ class Engine : public IEngine {
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     const int tot = nion * 3 * n;
     OFDFT_RUN("k_phases", st, (double)tot * 16, k_phases<<<std::min(4096, (tot + 255) / 256), 256, 0, st>>>(pos_d, nion, n, L, phases));
-    // Ewald splitting: reciprocal weights exp(-G^2/(4 eta^2)) below 1e-17 at g2max
-    const double gnyq = kPi * n / L;
-    const double g2max = std::min(g2cut_loc, gnyq * gnyq);
-    const double eta = std::sqrt(g2max / (4.0 * 39.0));
+    const double g2max = ewald_g2max();
+    const double eta = ewald_eta();
     const int full = S_out != nullptr;
     // rows are also kept out to |m|^2 = 600 for the S_ei shells
     const double g2rows = std::max(g2max, (2.0 * kPi / L) * (2.0 * kPi / L) * 600.0);
@@ -555,7 +578,7 @@ class Engine : public IEngine {
       OFDFT_CK(cudaMemsetAsync(Sg, 0, NH * sizeof(C), st));
       OFDFT_CK(cudaMemsetAsync(vloc, 0, NH * sizeof(C), st));
     }
-    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<nrows, 128, 0, st>>>(phases, Z_d, nion, n, L, cs.rc, eta, g2rows, full, mlim, Sg, vloc, partials));
+    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<nrows, 128, 0, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, Sg, vloc, partials));
     int rc;
     if ((rc = sum_partials(nrows, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;

@@ -34,9 +34,12 @@ static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n
 // the (kx, ky) phase products of a chunk of ions are staged in shared memory.
 // Rows whose smallest |G|^2 exceeds g2max are written as zero (their V_loc and
 // Ewald weights are below double precision) unless full != 0.
+// sf_tab[m^2] = (v~(G)/Omega per unit charge, (2 pi/Omega) exp(-G^2/(4 eta^2))/G^2),
+// the second 0 at m^2 = 0: both depend on |G| only and are tabulated once per
+// plan in FP64, so no exponential is evaluated here.
 template <typename T>
 __global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, const double* __restrict__ Z,
-                                                int n_ion, int n, double L, double rc, double eta_ew,
+                                                int n_ion, int n, double L, const double2* __restrict__ sf_tab,
                                                 double g2max, int full, int mlim,
                                                 cplx<T>* __restrict__ S_out, cplx<T>* __restrict__ vloc,
                                                 double* __restrict__ ew_partial) {
@@ -58,7 +61,6 @@ __global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, 
     kx = mx < 0 ? mx + n : mx; ky = my < 0 ? my + n : my;
   }
   const double tp = 2.0 * kPi / L;
-  const double Omega = L * L * L;
   const double g2row = tp * tp * (double)(mx * mx + my * my);
   const size_t rowoff = ((size_t)kx * n + ky) * nh;
   double ew = 0;
@@ -95,17 +97,11 @@ __global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, 
       }
       if (kz < nh) {
         const int m2 = mx * mx + my * my + kz * kz;
-        const double G2 = tp * tp * (double)m2;
         if (S_out) S_out[rowoff + kz] = mk<T>(sr, si);
-        double v;
-        if (m2 == 0) v = kPi * rc * rc;
-        else v = -4.0 * kPi * exp(-G2 * rc * rc / 4.0) / G2;
-        vloc[rowoff + kz] = mk<T>((T)(v * (double)zr / Omega), (T)(v * (double)zi / Omega));
-        if (m2 > 0) {
-          const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
-          ew += w * 2.0 * kPi / Omega * exp(-G2 / (4.0 * eta_ew * eta_ew)) / G2 *
-                ((double)zr * (double)zr + (double)zi * (double)zi);
-        }
+        const double2 f = sf_tab[m2];
+        vloc[rowoff + kz] = mk<T>((T)(f.x * (double)zr), (T)(f.x * (double)zi));
+        const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+        ew += w * f.y * ((double)zr * (double)zr + (double)zi * (double)zi);
       }
     }
   }
