@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--serving", type=int, default=0,
                     help="also run the serving loop on this many Poisson requests (0 = skip)")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--no-md", action="store_true", help="skip the MD time-per-step block")
     return ap.parse_args()
 
 
@@ -239,6 +240,8 @@ def run_ours(args, rank, world, local):
         res["batched"] = run_batched(args, dev)
     if args.serving > 0:
         res["serving"] = run_serving(args, dev)
+    if not args.no_md:
+        res["md"] = run_md(args, dev)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -280,6 +283,50 @@ def run_batched(args, dev):
     out["converged_sequential"] = sum(r["converged"] for r in seq)
     for p in plans:
         p.close()
+    return out
+
+
+# time per MD step the paper tabulates for its CPU runs (Methods, Table 2;
+# 8 cores of 2x Xeon Gold 6240R): context, not a target of this machine
+PAPER_MD_S_PER_STEP = {"md_H32_rs1": 0.08, "md_H14_rs2": 0.38, "md_H14_rs3.23": 2.39}
+
+
+def run_md(args, dev, warm=10, steps=50):
+    """Time per NVT MD step (electrons minimised from the previous density,
+    forces, Nose-Hoover Verlet step) for the paper's three hydrogen MD cells:
+    32 H at r_s = 1 (dt 0.02 fs), 14 H at r_s = 2 and 3.23 (dt 0.1 fs), theta = 1,
+    T_ion = T, thermostat period 100 dt.  Wall time around ofdft_md_run (it
+    synchronises), after `warm` equilibration steps."""
+    import numpy as np
+    import torch
+    import paper_2601_23002_gb300 as og
+    from workloads import hydrogen_md_cells, md_velocities, PROTON_MASS, SEED_BASE
+    fs = 1.0 / 2.4188843265857e-2          # hbar/E_h per femtosecond
+    out = {}
+    for i, cell in enumerate(hydrogen_md_cells()):
+        dt = (0.02 if cell.meta["rs"] == 1.0 else 0.1) * fs
+        mass = np.full(cell.n_ion, PROTON_MASS)
+        key = cell.label.rsplit("_n", 1)[0]
+        row = {"n": cell.n, "n_ion": cell.n_ion, "T_eV": cell.T * 27.211386245988, "dt_fs": dt / fs,
+               "paper_cpu_s_per_step": PAPER_MD_S_PER_STEP.get(key)}
+        for precision in ("fp32", "fp64"):
+            plan = og.plan_for_cell(cell, precision=precision)
+            rho = torch.empty(cell.n ** 3, dtype=torch.float32 if precision == "fp32" else torch.float64,
+                              device=dev)
+            kw = dict(T_ion=cell.T, tau=100 * dt, tol_F_per_ion=TOL_F, tol_residual=TOL_R)
+            vel = md_velocities(SEED_BASE + 7000 + i, mass, cell.T)
+            a = plan.md_run(rho, cell.pos, vel, mass, warm, dt, start_uniform=True, **kw)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            b = plan.md_run(rho, a["pos"], a["vel"], mass, steps, dt, thermostat=a["thermostat"], **kw)
+            t = time.perf_counter() - t0
+            plan.close()
+            row[precision] = {"ms_per_step": 1e3 * t / steps, "steps": steps,
+                              "evals_per_step": float(np.mean(b["frames"]["evaluations"])),
+                              "conserved_drift_per_ion": float(np.abs(b["frames"]["conserved"]
+                                                                      - b["frames"]["conserved"][0]).max()
+                                                               / cell.n_ion)}
+        out[cell.label] = row
     return out
 
 
@@ -457,6 +504,8 @@ def main():
         line["batched"] = res["batched"]
     if "serving" in res:
         line["serving"] = res["serving"]
+    if "md" in res:
+        line["md"] = res["md"]
     if world == 1 and not args.no_cpu_baseline:
         fallback = int(line.get("fp64", {}).get("evals_per_snapshot", r32["evals"] / args.steps))
         line["cpu_baseline"] = cpu_baseline(cell, fallback)
