@@ -235,3 +235,46 @@ def test_full_size_128_matches_converged_oracle(precision):
     dF = abs(out["F_total"] - ref["energies"]["total"]) / cell.n_ion
     print(f"{precision}: |F_gpu - F_oracle|/ion = {dF:.2e}")
     assert dF < 1e-6
+
+
+def test_full_size_256_1024_ions_terms_and_sei():
+    # 1024 Z=3 ions at r_s = 2.5, theta = 0.3 on 256^3, FP32 bulk (the largest
+    # single-cell workload): the GPU minimum converges with N_e exact; at that
+    # density the terms the oracle can form at this size (pointwise TF and XC,
+    # Hartree and vW by one transform each, Ewald) agree to 1e-5 Ha/ion, and
+    # S_ei on the first 200 shells agrees with the oracle's direct sum.
+    from oracle import fermi_dirac as fd, xc as oxc
+    from oracle.cell import ewald_energy, g2_grid
+    from oracle.functional import fft3, N_MIN
+    from oracle.sei import sei_shells_direct
+    cell = config_cell(4)
+    plan = og.plan_for_cell(cell, precision="fp32")
+    rho = torch.empty(cell.n ** 3, dtype=torch.float32, device="cuda")
+    out = plan.minimize(rho, start_uniform=True)
+    assert out["converged"], out
+    assert abs(out["N_e"] - cell.n_electrons) < 1e-4 * cell.n_electrons
+    q, s = plan.sei_shells(rho, 200)
+    plan.close()
+    n_np = rho.double().cpu().numpy().reshape((cell.n,) * 3)
+    del rho
+    Om, N, T = cell.volume, cell.n ** 3, cell.T
+    dV = Om / N
+    nf = np.maximum(n_np, N_MIN)
+    f, _, _ = fd.tf_free_energy_density(nf, T)
+    exc, _ = oxc.lda_xc(nf)
+    nt = fft3(n_np)
+    G2 = g2_grid(cell.n, cell.L)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        coul = np.where(G2 > 0, 4 * math.pi / np.where(G2 > 0, G2, 1.0), 0.0)
+    ref = {"F_TF": dV * float(np.sum(f)), "E_xc": dV * float(np.sum(n_np * exc)),
+           "E_H": 0.5 * Om * float(np.sum(coul * np.abs(nt) ** 2)),
+           "E_vW": 0.5 * Om * float(np.sum(G2 * np.abs(fft3(np.sqrt(n_np))) ** 2)),
+           "E_ion": ewald_energy(np.asarray(cell.Z, float), cell.pos, cell.L)}
+    del nt, G2, coul
+    for k, v in ref.items():
+        print(f"{k}: gpu {out[k]:.8f} oracle {v:.8f}")
+        assert abs(out[k] - v) / cell.n_ion < 1e-5, k
+    qr, sr = sei_shells_direct(n_np, cell.pos, cell.L, cell.n_electrons, 200)
+    assert np.allclose(q, qr, rtol=1e-12)
+    print("S_ei max |diff|", np.abs(s - sr).max(), "max |S|", np.abs(sr).max())
+    assert np.abs(s - sr).max() < 1e-4 * max(1.0, np.abs(sr).max())

@@ -122,3 +122,14 @@ def test_sii_simple_cubic_lattice_counts_reciprocal_vectors():
     ref = np.array([M ** 3 * hit[k] / count[k] for k in keys])
     assert np.allclose(q, 2 * math.pi / L * np.sqrt(keys), rtol=1e-15)
     assert np.allclose(s, ref, atol=1e-10)
+
+
+def test_sei_direct_equals_full_grid_form():
+    from oracle.sei import sei_shells_direct
+    c = random_cell(23, 11, 1.0, 1.7, 1.0, 20)
+    rng = np.random.default_rng(4)
+    rho = c.n_electrons / c.volume * (1 + 0.2 * rng.random((20,) * 3))
+    q1, s1 = sei_shells(rho, c.pos, c.L, c.n_electrons, 50)
+    q2, s2 = sei_shells_direct(rho, c.pos, c.L, c.n_electrons, 50)
+    assert np.allclose(q1, q2, rtol=1e-15)
+    assert np.abs(s1 - s2).max() < 1e-12 * max(1.0, np.abs(s1).max())
