@@ -652,7 +652,7 @@ class Engine : public IEngine {
   int precondition(const T* in, T* out, cudaStream_t st, const T* pold = nullptr, T* pyout = nullptr) {
     Spectra<T> sp{};
     sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = planes ? 1 : 0;
-    ProArgs<T> pa{1, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)0};
+    ProArgs<T> pa{1, nullptr, in, nullptr, (T)0, (T)1, (T)cs.alpha, (T)0};
     const double tp = 2.0 * kPi / L;
     using TV = typename TreeVal<T>::type;
     TV* pt = reinterpret_cast<TV*>(partials);
@@ -671,7 +671,7 @@ class Engine : public IEngine {
     FinArgs<T> fa{pt, 0, pe, 0, res_d};
     EpiArgs<T> ea{3, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)Te, (T)1, (T)0, cs.terms, out, pe, fa,
                   counters + 0, pold, pyout};
-    OFDFT_RUN("k_zinv_epi", st, (double)NH * sizeof(C) + (double)N * sizeof(T), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+    OFDFT_RUN("k_zinv_epi", st, (double)NH * sizeof(C) + (double)N * sizeof(T) * (pyout ? 3.0 : 1.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     return OFDFT_OK;
   }
 

@@ -215,10 +215,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
   const size_t off = row0 * n;
   const int tot = R * n;
   // all of the block's input rows in flight at once
+  // (mode 1 with d == nullptr: the field is psi itself, as in the
+  // preconditioning pass)
   const T* src0 = a.mode == 0 ? a.rho : a.psi;
+  const bool has_d = a.mode != 0 && a.d != nullptr;
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
     cp_async<sizeof(T)>(psit + q, src0 + off + q, true);
-    if (a.mode != 0) cp_async<sizeof(T)>(dbuf + q, a.d + off + q, true);
+    if (has_d) cp_async<sizeof(T)>(dbuf + q, a.d + off + q, true);
   }
   cp_async_commit();
   cp_async_wait<0>();
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
     const T x = psit[q];
     if (a.mode == 0) { dbuf[q] = x; psit[q] = sqrt(fmax(x, (T)0)); }
-    else psit[q] = x + tstep * dbuf[q];
+    else if (has_d) psit[q] = x + tstep * dbuf[q];
   }
   __syncthreads();
   const T scale = a.dsc ? (T)a.dsc[0] : a.scale, alpha = a.alpha, nmin = (T)kNmin;
@@ -582,10 +585,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
     // so every row starts on an 8-byte boundary)
     constexpr int E = 8 / sizeof(T);
     const int pieces = tot / E;
-    const T* src0 = a.mode == 0 ? a.rho : a.psi;
-    for (int q = threadIdx.x; q < (a.mode == 3 ? 0 : pieces); q += blockDim.x) {
+    // (mode 3: the previous output pold, when P y = out - pold is wanted)
+    const T* src0 = a.mode == 0 ? a.rho : (a.mode == 3 ? a.pold : a.psi);
+    const int npc = a.mode == 3 ? (a.pyout ? pieces : 0) : pieces;
+    for (int q = threadIdx.x; q < npc; q += blockDim.x) {
       cp_async<8>(pin + q * E, src0 + off + q * E, true);
-      if (a.mode != 0) cp_async<8>(pin + (size_t)Rfull * n + q * E, a.d + off + q * E, true);
+      if (a.mode == 1) cp_async<8>(pin + (size_t)Rfull * n + q * E, a.d + off + q * E, true);
     }
   }
   cp_async_commit();
@@ -624,7 +629,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
     for (int q = threadIdx.x; q < tot; q += blockDim.x) {
       const T v = fP[q];
       a.out[off + q] = v;
-      if (a.pyout) a.pyout[off + q] = v - a.pold[off + q];
+      if (a.pyout) a.pyout[off + q] = v - pin[q];
     }
     return;
   }
