@@ -166,6 +166,19 @@ int ofdft_energy_potential(ofdft_plan* plan, const void* rho, void* v_out,
                            ofdft_energies* e_out, void* stream);
 
 /*
+ * As ofdft_energy_potential, without a host round trip: the energies are
+ * formed on the device and written to e_dev (device memory, 11 doubles in the
+ * order of ofdft_energies: F_TF, E_vW, E_NL, E_H, E_loc, E_xc, E_ion, F_total,
+ * N_e, mu, residual), stream-ordered after the potential.  Does not
+ * synchronise `stream`; the caller reads e_dev after its own synchronisation
+ * (e.g. to keep a sequence of evaluations queued on the GPU).  The caller owns
+ * e_dev; the plan's internal reduction buffers are reused by the next call on
+ * the plan, so calls on one plan are ordered on one stream.
+ */
+int ofdft_energy_potential_async(ofdft_plan* plan, const void* rho, void* v_out, double* e_dev,
+                                 void* stream);
+
+/*
  * Minimise F over n = N_e psi^2 / int psi^2 by L-BFGS with a strong-Wolfe line
  * search.  rho_io: device real field; on entry the initial density (or NULL
  * contents ignored when start_uniform != 0, which starts from the uniform

@@ -76,7 +76,7 @@ EXPORTS = ["ofdft_default_opts", "ofdft_default_min_opts", "ofdft_last_error", "
            "ofdft_energy_potential", "ofdft_minimize", "ofdft_sei_shells",
            "ofdft_profile_enable", "ofdft_profile_read", "ofdft_sei_shells_static",
            "ofdft_minimize_batch", "ofdft_autotune", "ofdft_set_tiles", "ofdft_forces",
-           "ofdft_pressure", "ofdft_md_run"]
+           "ofdft_pressure", "ofdft_md_run", "ofdft_energy_potential_async"]
 
 _lib = None
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     L.ofdft_forces.restype = ctypes.c_int
     L.ofdft_pressure.argtypes = [vp, vp, c_double_p, vp]
     L.ofdft_pressure.restype = ctypes.c_int
+    L.ofdft_energy_potential_async.argtypes = [vp, vp, vp, vp, vp]
+    L.ofdft_energy_potential_async.restype = ctypes.c_int
     L.ofdft_md_run.argtypes = [vp, vp, ctypes.c_int, c_double_p, c_double_p, c_double_p,
                                ctypes.POINTER(MdOpts), ctypes.POINTER(MdThermostat), ctypes.c_int,
                                ctypes.POINTER(MdFrame), c_double_p, c_double_p, c_double_p, vp]

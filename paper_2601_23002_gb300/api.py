@@ -98,6 +98,22 @@ class Plan:
                                                _stream_ptr(self.stream)))
         return e.as_dict()
 
+    ENERGY_KEYS = ("F_TF", "E_vW", "E_NL", "E_H", "E_loc", "E_xc", "E_ion", "F_total", "N_e", "mu", "residual")
+
+    def energy_potential_async(self, rho: torch.Tensor, v_out: torch.Tensor | None = None,
+                               e_out: torch.Tensor | None = None) -> torch.Tensor:
+        """Queue one evaluation (ofdft_energy_potential_async); returns the
+        device tensor (float64 [11], order of ENERGY_KEYS) the energies are
+        written to, without synchronising the stream."""
+        if e_out is None:
+            e_out = torch.empty(11, dtype=torch.float64, device=rho.device)
+        if not (e_out.is_cuda and e_out.dtype == torch.float64 and e_out.is_contiguous() and e_out.numel() >= 11):
+            raise ValueError("e_out must be a contiguous CUDA float64 tensor with 11 elements")
+        vp = self._field(v_out, "v_out") if v_out is not None else None
+        _check(self.lib.ofdft_energy_potential_async(self._p, self._field(rho, "rho"), vp,
+                                                     ctypes.c_void_p(e_out.data_ptr()), _stream_ptr(self.stream)))
+        return e_out
+
     def minimize(self, rho: torch.Tensor, start_uniform: bool = True, tol_F_per_ion: float = 1e-6,
                  tol_residual: float = 1e-4, m: int = 8, max_iter: int = 1000, c1: float = 1e-4,
                  c2: float = 0.9, raise_on_fail: bool = False) -> dict:
@@ -219,6 +235,23 @@ def minimize_batch(plans, rhos, concurrency: int = 8, start_uniform: bool = True
                  converged=res[i].status == C.OFDFT_OK)
         out.append(d)
     return out
+
+
+def minimize(cell, rho: torch.Tensor | None = None, precision: str = "fp64", device="cuda", **opts):
+    """One snapshot end to end: plan + structure factor for `cell` (a
+    workloads.Cell or any object with L, n, Z, pos, rc, T), minimisation from
+    `rho` (a density on the device) or from the uniform density, plan freed.
+    Returns (converged density, result dict)."""
+    plan = plan_for_cell(cell, precision=precision)
+    try:
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        out = torch.empty(cell.n ** 3, dtype=dt, device=device)
+        if rho is not None:
+            out.copy_(rho.reshape(-1))
+        res = plan.minimize(out, start_uniform=rho is None, **opts)
+    finally:
+        plan.close()
+    return out, res
 
 
 def plan_for_cell(cell, precision="fp64", terms=C.TERMS_ALL, alpha=0.5, stream=None) -> Plan:

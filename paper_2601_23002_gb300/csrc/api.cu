@@ -162,6 +162,11 @@ int ofdft_energy_potential(ofdft_plan* plan, const void* rho, void* v_out, ofdft
   return plan->eng->energy_potential(rho, v_out, e_out, stream);
 }
 
+int ofdft_energy_potential_async(ofdft_plan* plan, const void* rho, void* v_out, double* e_dev, void* stream) {
+  if (!plan || !rho || !e_dev) { set_error("plan, rho and e_dev must not be NULL"); return OFDFT_ERR_INVALID; }
+  return plan->eng->energy_potential_async(rho, v_out, e_dev, stream);
+}
+
 int ofdft_minimize(ofdft_plan* plan, void* rho_io, int start_uniform, const ofdft_min_opts* o, ofdft_result* r,
                    void* stream) {
   if (!plan || !rho_io) { set_error("plan and rho_io must not be NULL"); return OFDFT_ERR_INVALID; }

@@ -25,6 +25,7 @@ class IEngine {
   virtual int create(void* stream) = 0;
   virtual int set_ions(const double* pos, int on_device, void* S_out, void* stream) = 0;
   virtual int energy_potential(const void* rho, void* v_out, ofdft_energies* e, void* stream) = 0;
+  virtual int energy_potential_async(const void* rho, void* v_out, double* e_dev, void* stream) = 0;
   virtual int minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o, ofdft_result* r,
                        void* stream) = 0;
   virtual int sei_shells(const void* rho, int n_shells, double* q_out, double* s_out, void* stream) = 0;

@@ -711,6 +711,15 @@ class Engine : public IEngine {
     return OFDFT_OK;
   }
 
+  int energy_potential_async(const void* rho, void* v_out, double* e_dev, void* stream_) override {
+    if (!ions_set) { set_error("ofdft_structure_factor must be called before evaluations"); return OFDFT_ERR_INVALID; }
+    cudaStream_t st = (cudaStream_t)stream_;
+    int rc = eval(0, (const T*)rho, nullptr, nullptr, 0.0, 1.0, 0.0, 0.0, (T*)v_out, st, false);
+    if (rc) return rc;
+    OFDFT_RUN("k_finish_energies", st, 23 * 8.0, k_finish_energies<<<1, 32, 0, st>>>(res_d, dV, E_ion, merged() ? 1 : 0, e_dev));
+    return OFDFT_OK;
+  }
+
   void fill_energies(ofdft_energies* e) const {
     e->F_TF = res_h[0]; e->E_vW = res_h[1]; e->E_NL = res_h[2]; e->E_H = res_h[3];
     e->E_loc = res_h[4]; e->E_xc = res_h[5]; e->E_ion = res_h[6]; e->F_total = res_h[7];

@@ -498,3 +498,24 @@ __global__ void __launch_bounds__(256) k_pressure_g(const cplx<T>* __restrict__ 
 }
 
 }  // namespace ofdft
+
+namespace ofdft {
+
+// The energies of a density evaluation (mode 0) from its raw sums raw[0..11]
+// (see finalize_eval), written to e[0..10] in the order of ofdft_energies:
+// F_TF, E_vW, E_NL, E_H, E_loc, E_xc, E_ion, F_total, N_e, mu, residual.
+// One thread; the same arithmetic as the host's finish for mode 0.
+static __global__ void k_finish_energies(const double* __restrict__ raw, double dV, double E_ion, int merged,
+                                         double* __restrict__ e) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double E_H = raw[0], E_loc = raw[1], E_NL = raw[2], E_vW = raw[3];
+  const double F_TF = raw[4] * dV, E_xc = raw[5] * dV, vn = raw[6] * dV + (merged ? E_NL : 0.0);
+  const double gg = raw[8] * dV, gpsi = raw[9] * dV, ne = raw[10] * dV;
+  const double mu = (vn + E_vW) / ne;
+  const double r2 = (gg - 2.0 * mu * gpsi + mu * mu * ne) / ne;
+  e[0] = F_TF; e[1] = E_vW; e[2] = E_NL; e[3] = E_H; e[4] = E_loc; e[5] = E_xc; e[6] = E_ion;
+  e[7] = F_TF + E_vW + E_NL + E_H + E_loc + E_xc + E_ion;
+  e[8] = ne; e[9] = mu; e[10] = sqrt(fmax(r2, 0.0));
+}
+
+}  // namespace ofdft

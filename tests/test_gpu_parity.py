@@ -278,3 +278,40 @@ def test_full_size_256_1024_ions_terms_and_sei():
     assert np.allclose(q, qr, rtol=1e-12)
     print("S_ei max |diff|", np.abs(s - sr).max(), "max |S|", np.abs(sr).max())
     assert np.abs(s - sr).max() < 1e-4 * max(1.0, np.abs(sr).max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_async_energies_equal_the_synchronous_ones(precision):
+    # ofdft_energy_potential_async forms the energies on the device; queued
+    # back to back on one stream they match the synchronous call's
+    cell = CASES[2][1]()
+    plan = og.plan_for_cell(cell, precision=precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    rhos = [torch.tensor(rand_density(cell, s), dtype=dt, device="cuda").reshape(-1) for s in (41, 42)]
+    e_dev = [plan.energy_potential_async(r) for r in rhos]
+    v = torch.empty_like(rhos[0])
+    e_dev.append(plan.energy_potential_async(rhos[0], v_out=v))
+    torch.cuda.synchronize()
+    for r, ed in zip(rhos + rhos[:1], e_dev):
+        ref = plan.energy_potential(r)
+        got = dict(zip(og.Plan.ENERGY_KEYS, ed.cpu().tolist()))
+        for k in og.Plan.ENERGY_KEYS:
+            assert abs(got[k] - ref[k]) <= 1e-13 * max(1.0, abs(ref[k])), (k, got[k], ref[k])
+    vr = torch.empty_like(v)
+    plan.energy_potential(rhos[0], vr)
+    assert torch.equal(v, vr)
+    plan.close()
+
+
+def test_module_level_minimize_matches_the_plan():
+    cell = fcc_cell(n=16)
+    rho, res = og.minimize(cell, tol_F_per_ion=1e-10, tol_residual=1e-7)
+    assert res["converged"] and rho.numel() == 16 ** 3
+    plan = og.plan_for_cell(cell)
+    r2 = torch.empty_like(rho)
+    ref = plan.minimize(r2, start_uniform=True, tol_F_per_ion=1e-10, tol_residual=1e-7)
+    plan.close()
+    assert res["F_total"] == ref["F_total"] and torch.equal(rho, r2)
+    # a warm start from the converged density stays there
+    rho3, res3 = og.minimize(cell, rho=rho, tol_F_per_ion=1e-10, tol_residual=1e-7)
+    assert res3["converged"] and abs(res3["F_total"] - res["F_total"]) < 1e-9
