@@ -578,9 +578,13 @@ class Engine : public IEngine {
       OFDFT_CK(cudaMemsetAsync(Sg, 0, NH * sizeof(C), st));
       OFDFT_CK(cudaMemsetAsync(vloc, 0, NH * sizeof(C), st));
     }
-    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<nrows, 128, 0, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, Sg, vloc, partials));
+    // ions per shared-memory chunk: staged kz phases within 40 KB
+    const int sch = std::max(1, std::min(64, (int)(40960 / ((size_t)nh * sizeof(C)))));
+    const size_t ssm = (size_t)sch * nh * sizeof(C) + (size_t)kStructRows * sch * sizeof(C) + (size_t)sch * sizeof(T);
+    const int sgrid = (nrows + kStructRows - 1) / kStructRows;
+    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, partials));
     int rc;
-    if ((rc = sum_partials(nrows, 1, 0, st))) return rc;
+    if ((rc = sum_partials(sgrid, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
     const int nimg = (int)std::ceil(rcut / L) + 1;
     ew_eta = eta; ew_rcut = rcut; ew_nimg = nimg;

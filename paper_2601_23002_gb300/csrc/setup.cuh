@@ -30,79 +30,116 @@ static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n
 // S(G) = sum_I exp(-i G.R_I) and S_Z(G) = sum_I Z_I exp(-i G.R_I) on the half
 // spectrum; V_loc(G) = (1/Omega) v~(G) S_Z(G) with the common smoothing radius
 // rc; the Ewald reciprocal sum (2 pi / Omega) sum_{G != 0} exp(-G^2/4eta^2)/G^2
-// |S_Z|^2 accumulated on the way.  One block per (kx, ky) row, threads over kz;
-// the (kx, ky) phase products of a chunk of ions are staged in shared memory.
-// Rows whose smallest |G|^2 exceeds g2max are written as zero (their V_loc and
-// Ewald weights are below double precision) unless full != 0.
-// sf_tab[m^2] = (v~(G)/Omega per unit charge, (2 pi/Omega) exp(-G^2/(4 eta^2))/G^2),
+// |S_Z|^2 accumulated on the way.  A block takes kStructRows (kx, ky) rows, one
+// per warp, lanes over kz; the ions go in chunks of ch, whose kz phases are
+// staged in shared memory once for all rows of the block (with the rows' (kx,
+// ky) phase products).  Rows whose smallest |G|^2 exceeds g2max are written as
+// zero (their V_loc and Ewald weights are below double precision) unless
+// full != 0.
+//   sf_tab[m^2] = (v~(G)/Omega per unit charge, (2 pi/Omega) exp(-G^2/(4 eta^2))/G^2),
 // the second 0 at m^2 = 0: both depend on |G| only and are tabulated once per
 // plan in FP64, so no exponential is evaluated here.
+// Shared memory: ez[ch][nh] | xy[kStructRows][ch] (complex) | zz[ch] (T).
+constexpr int kStructRows = 8;
+constexpr int kStructMaxKJ = 9;     // kz per lane: nh <= 32 * 9
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_struct(const double2* __restrict__ ph, const double* __restrict__ Z,
-                                                int n_ion, int n, double L, const double2* __restrict__ sf_tab,
-                                                double g2max, int full, int mlim,
-                                                cplx<T>* __restrict__ S_out, cplx<T>* __restrict__ vloc,
-                                                double* __restrict__ ew_partial) {
-  constexpr int CH = 128;
-  __shared__ cplx<T> sxy[CH];
-  __shared__ T szz[CH];
+__global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __restrict__ ph,
+                                                             const double* __restrict__ Z, int n_ion, int n,
+                                                             double L, const double2* __restrict__ sf_tab,
+                                                             double g2max, int full, int mlim, int ch,
+                                                             cplx<T>* __restrict__ S_out,
+                                                             cplx<T>* __restrict__ vloc,
+                                                             double* __restrict__ ew_partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const int nh = n / 2 + 1;
-  // mlim < 0: one block per row (kx, ky) of the grid; mlim >= 0: one block per
-  // row with |mx|, |my| <= mlim (the caller has zeroed the other rows)
-  int kx, ky, mx, my;
-  if (mlim < 0) {
-    kx = blockIdx.x / n; ky = blockIdx.x % n;
-    mx = kx <= n / 2 - 1 ? kx : kx - n;
-    my = ky <= n / 2 - 1 ? ky : ky - n;
-  } else {
-    const int side = 2 * mlim + 1;
-    mx = (int)(blockIdx.x / side) - mlim; my = (int)(blockIdx.x % side) - mlim;
-    kx = mx < 0 ? mx + n : mx; ky = my < 0 ? my + n : my;
-  }
-  const double tp = 2.0 * kPi / L;
-  const double g2row = tp * tp * (double)(mx * mx + my * my);
-  const size_t rowoff = ((size_t)kx * n + ky) * nh;
-  double ew = 0;
-  if (!full && g2row > g2max) {
-    for (int kz = threadIdx.x; kz < nh; kz += blockDim.x) {
-      if (S_out) S_out[rowoff + kz] = mk<T>(0, 0);
-      vloc[rowoff + kz] = mk<T>(0, 0);
+  cplx<T>* ez = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* sxy = ez + (size_t)ch * nh;
+  T* szz = reinterpret_cast<T*>(sxy + (size_t)kStructRows * ch);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // mlim < 0: every (kx, ky) row of the grid; mlim >= 0: the rows with |mx|,
+  // |my| <= mlim (the caller has zeroed the other rows)
+  const int side = 2 * mlim + 1;
+  const int nrows = mlim < 0 ? n * n : side * side;
+  auto row_of = [&](int rw, int& kx, int& ky, int& mx, int& my) {
+    if (mlim < 0) {
+      kx = rw / n; ky = rw % n;
+      mx = kx <= n / 2 - 1 ? kx : kx - n;
+      my = ky <= n / 2 - 1 ? ky : ky - n;
+    } else {
+      mx = rw / side - mlim; my = rw % side - mlim;
+      kx = mx < 0 ? mx + n : mx; ky = my < 0 ? my + n : my;
     }
-  } else {
-    for (int kz0 = 0; kz0 < nh; kz0 += blockDim.x) {
-      const int kz = kz0 + threadIdx.x;
-      T sr = 0, si = 0, zr = 0, zi = 0;
-      for (int I0 = 0; I0 < n_ion; I0 += CH) {
-        const int cnt = min(CH, n_ion - I0);
-        __syncthreads();
-        for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
-          const int I = I0 + c;
-          const double2 ex = ph[((size_t)I * 3 + 0) * n + kx];
-          const double2 ey = ph[((size_t)I * 3 + 1) * n + ky];
-          sxy[c] = mk<T>((T)(ex.x * ey.x - ex.y * ey.y), (T)(ex.x * ey.y + ex.y * ey.x));
-          szz[c] = (T)Z[I];
-        }
-        __syncthreads();
-        if (kz < nh) {
-          for (int c = 0; c < cnt; ++c) {
-            const double2 ezd = ph[((size_t)(I0 + c) * 3 + 2) * n + kz];
-            const T ezr = (T)ezd.x, ezi = (T)ezd.y;
-            const cplx<T> xy = sxy[c];
-            const T pr = xy.x * ezr - xy.y * ezi, pi = xy.x * ezi + xy.y * ezr;
-            sr += pr; si += pi;
-            zr += szz[c] * pr; zi += szz[c] * pi;
+  };
+  const int row = blockIdx.x * kStructRows + warp;
+  int kx = 0, ky = 0, mx = 0, my = 0;
+  const bool valid = row < nrows;
+  if (valid) row_of(row, kx, ky, mx, my);
+  const double tp = 2.0 * kPi / L;
+  const bool skip = !full && tp * tp * (double)(mx * mx + my * my) > g2max;
+  T sr[kStructMaxKJ], si[kStructMaxKJ], zr[kStructMaxKJ], zi[kStructMaxKJ];
+#pragma unroll
+  for (int j = 0; j < kStructMaxKJ; ++j) { sr[j] = 0; si[j] = 0; zr[j] = 0; zi[j] = 0; }
+  for (int I0 = 0; I0 < n_ion; I0 += ch) {
+    const int cnt = min(ch, n_ion - I0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt * nh; q += blockDim.x) {
+      const int c = q / nh, kz = q - c * nh;
+      const double2 e = ph[((size_t)(I0 + c) * 3 + 2) * n + kz];
+      ez[q] = mk<T>((T)e.x, (T)e.y);
+    }
+    for (int q = threadIdx.x; q < kStructRows * cnt; q += blockDim.x) {
+      const int r = q / cnt, c = q - r * cnt;
+      const int rw = blockIdx.x * kStructRows + r;
+      cplx<T> v = mk<T>((T)0, (T)0);
+      if (rw < nrows) {
+        int qx, qy, px, py;
+        row_of(rw, qx, qy, px, py);
+        const double2 ex = ph[((size_t)(I0 + c) * 3 + 0) * n + qx];
+        const double2 ey = ph[((size_t)(I0 + c) * 3 + 1) * n + qy];
+        v = mk<T>((T)(ex.x * ey.x - ex.y * ey.y), (T)(ex.x * ey.y + ex.y * ey.x));
+      }
+      sxy[r * ch + c] = v;
+    }
+    for (int c = threadIdx.x; c < cnt; c += blockDim.x) szz[c] = (T)Z[I0 + c];
+    __syncthreads();
+    if (valid && !skip) {
+      for (int c = 0; c < cnt; ++c) {
+        const cplx<T> xy = sxy[warp * ch + c];
+        const T zc = szz[c];
+        const cplx<T>* e = ez + (size_t)c * nh;
+#pragma unroll
+        for (int j = 0; j < kStructMaxKJ; ++j) {
+          const int kz = lane + 32 * j;
+          if (kz < nh) {
+            const cplx<T> w = e[kz];
+            const T pr = xy.x * w.x - xy.y * w.y, pi = xy.x * w.y + xy.y * w.x;
+            sr[j] += pr; si[j] += pi;
+            zr[j] += zc * pr; zi[j] += zc * pi;
           }
         }
       }
-      if (kz < nh) {
-        const int m2 = mx * mx + my * my + kz * kz;
-        if (S_out) S_out[rowoff + kz] = mk<T>(sr, si);
-        const double2 f = sf_tab[m2];
-        vloc[rowoff + kz] = mk<T>((T)(f.x * (double)zr), (T)(f.x * (double)zi));
-        const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
-        ew += w * f.y * ((double)zr * (double)zr + (double)zi * (double)zi);
+    }
+  }
+  double ew = 0;
+  if (valid) {
+    const size_t rowoff = ((size_t)kx * n + ky) * nh;
+#pragma unroll
+    for (int j = 0; j < kStructMaxKJ; ++j) {
+      const int kz = lane + 32 * j;
+      if (kz >= nh) continue;
+      if (skip) {
+        if (S_out) S_out[rowoff + kz] = mk<T>(0, 0);
+        vloc[rowoff + kz] = mk<T>(0, 0);
+        continue;
       }
+      const int m2 = mx * mx + my * my + kz * kz;
+      if (S_out) S_out[rowoff + kz] = mk<T>(sr[j], si[j]);
+      const double2 f = sf_tab[m2];
+      vloc[rowoff + kz] = mk<T>((T)(f.x * (double)zr[j]), (T)(f.x * (double)zi[j]));
+      const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
+      ew += w * f.y * ((double)zr[j] * (double)zr[j] + (double)zi[j] * (double)zi[j]);
     }
   }
   double v[1] = {ew}, out[1];
