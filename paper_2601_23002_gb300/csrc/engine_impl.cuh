@@ -53,6 +53,10 @@ __global__ void k_convert_table(const double* __restrict__ a, T* __restrict__ b,
   if (i < cnt) b[i] = (T)a[i];
 }
 constexpr int kMaxMem = 16;
+// res_d / res_h: 0..13 evaluation, 16..119 Gram and direction dots, 120..125
+// k_accept's dots, 126..128 the device-formed trial (scale, psi shift, t),
+// 129..130 the device recursion's gamma and pairs used
+constexpr int kResSlots = 160;
 
 // ring slot of the i-th oldest history pair
 struct Ring {
@@ -110,6 +114,7 @@ class Engine : public IEngine {
   double* partials = nullptr;
   size_t partials_cap = 0;
   double* res_d = nullptr;
+  TwoLoopState* tl_state = nullptr;   // L-BFGS history scalars on the device
   double* res_h = nullptr;     // pinned
   unsigned int* counters = nullptr;   // last-block arrival counters (0 between launches)
   double* pos_d = nullptr;
@@ -352,11 +357,12 @@ class Engine : public IEngine {
                                      ((size_t)n * nh + 7) / 8 * 12 + ((size_t)n * n + 7) / 8 * 8,
                                      (size_t)grid_vec * kMaxV * kMaxW, (size_t)n * n, (size_t)4096});
     if ((rc = alloc(&partials, partials_cap))) return rc;
-    if ((rc = alloc(&res_d, 128))) return rc;
+    if ((rc = alloc(&res_d, kResSlots))) return rc;
+    if ((rc = alloc(&tl_state, 1))) return rc;
     if ((rc = alloc(&counters, 8))) return rc;
     OFDFT_CK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), st));
-    OFDFT_CK(cudaMemsetAsync(res_d, 0, 128 * sizeof(double), st));
-    OFDFT_CK(cudaMallocHost(&res_h, 128 * sizeof(double)));
+    OFDFT_CK(cudaMemsetAsync(res_d, 0, kResSlots * sizeof(double), st));
+    OFDFT_CK(cudaMallocHost(&res_h, kResSlots * sizeof(double)));
     if ((rc = alloc(&pos_d, (size_t)cs.Z.size() * 3))) return rc;
     if ((rc = alloc(&Z_d, cs.Z.size()))) return rc;
     if ((rc = alloc(&phases, (size_t)cs.Z.size() * 3 * n))) return rc;
@@ -733,7 +739,7 @@ class Engine : public IEngine {
   // ------------------------------------------------------------------
   // dot products <V_i, W_j> for host-side use (chunks of kMaxV vectors)
   int gram(const std::vector<const T*>& V, const std::vector<const T*>& W, std::vector<double>& out,
-           cudaStream_t st) {
+           cudaStream_t st, bool readback = true) {
     const int nv = (int)V.size(), nw = (int)W.size();
     if ((size_t)nv * nw > 104 || nw > kMaxW) { set_error("gram: too many vectors"); return OFDFT_ERR_INVALID; }
     out.assign((size_t)nv * nw, 0.0);
@@ -765,6 +771,7 @@ class Engine : public IEngine {
       prof.end(st);
       OFDFT_LAUNCH_CK();
     }
+    if (!readback) return OFDFT_OK;
     int rc;
     if ((rc = read_results(st))) return rc;
     for (int i = 0; i < nv; ++i)
@@ -775,14 +782,14 @@ class Engine : public IEngine {
   // out = sum_i c_i V_i; returns <out,out>, <out,g>, <out,psi> (times dV);
   // with dd == nullptr the dots are not read back (no host synchronisation)
   int lincomb(const VecList<T>& terms, T* out, double* dd, double* dg, double* dpsi, cudaStream_t st,
-              TrialScale ts = TrialScale{}) {
+              TrialScale ts = TrialScale{}, const double* dcoef = nullptr) {
     VecList<T> xl = terms;
     const int nv = terms.nv;
     xl.v[nv] = g; xl.v[nv + 1] = psi;
     xl.nv = nv + 2;
     OFDFT_RUN("k_lincomb", st, (double)(nv + 3) * N * sizeof(T),
               k_lincomb<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(kMaxLin - 1), nv + 2), st>>>(
-                  xl, nv, out, N, partials, counters + 2, res_d + 16, ts));
+                  xl, nv, out, N, partials, counters + 2, res_d + 16, ts, dcoef));
     if (!dd) return OFDFT_OK;
     int rc;
     if ((rc = read_results(st))) return rc;
@@ -913,13 +920,6 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
   if ((rc = precondition(g, pgv[pcur], st))) return rc;
 
   Ring ring; ring.m = m;
-  std::vector<double> SY((size_t)kMaxMem * kMaxMem, 0.0), YY((size_t)kMaxMem * kMaxMem, 0.0);
-  std::vector<double> YPY((size_t)kMaxMem * kMaxMem, 0.0);    // <y_a, P y_b>
-  std::vector<double> Sgv(kMaxMem, 0.0), Ygv(kMaxMem, 0.0);   // <s_slot, g>, <y_slot, g> for the current g
-  std::vector<double> YPg(kMaxMem, 0.0);                      // <y_slot, P g>
-  auto sy = [&](int a, int b) -> double& { return SY[(size_t)a * kMaxMem + b]; };
-  auto yy = [&](int a, int b) -> double& { return YY[(size_t)a * kMaxMem + b]; };
-  auto ypy = [&](int a, int b) -> double& { return YPY[(size_t)a * kMaxMem + b]; };
   double gg = 0;
   {
     std::vector<double> d0;
@@ -931,6 +931,23 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
   int small = 0, it = 0;
   bool converged = false;
   for (it = 1; it <= o.max_iter; ++it) {
+    double dd = 0, dg = 0, dpsi = 0, gamma = 1.0, t0 = 1.0;
+    // with history the direction is formed from device scalars and its first
+    // trial is launched right behind it; the host reads the direction's dots,
+    // the trial's result and the recursion's outcome in one round trip
+    bool first_ready = false;
+    double first_t = 0, first_f = 0, first_slope = 0, first_E[14], first_scale = 0, first_mu = 0;
+    // d = -P g (restart or first iteration); t0 = 10% of |psi| along it
+    auto steepest = [&]() -> int {
+      VecList<T> vl{};
+      vl.nv = 1;
+      vl.v[0] = pgv[pcur]; vl.c[0] = -1.0;
+      int e;
+      if ((e = lincomb(vl, d, &dd, &dg, &dpsi, st))) return e;
+      t0 = 0.1 * std::sqrt(Qcur / std::max(dd, 1e-300));
+      gamma = 1.0;
+      return OFDFT_OK;
+    };
     if (new_slot >= 0) {
       // P g of the new gradient, and P y_new = P g_new - P g_old on the way
       const int pnew = 1 - pcur;
@@ -938,116 +955,66 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       pcur = pnew;
       // the accepted pair's own dots came from k_accept (res 120..125); one
       // pass dots [older s, older y, y_new] with [g, P g, s_new, y_new, P y_new]
-      std::vector<int> old;
-      for (int i = 0; i < ring.count; ++i)
-        if (ring.slot(i) != new_slot) old.push_back(ring.slot(i));
-      const int no = (int)old.size();
+      TwoLoopArgs ta{};
+      ta.count = ring.count; ta.new_slot = new_slot; ta.dv = dV;
       std::vector<const T*> V;
-      for (int sl : old) V.push_back(Sh[sl]);
-      for (int sl : old) V.push_back(Yh[sl]);
+      for (int i = 0; i < ring.count; ++i) {
+        ta.ring_slot[i] = ring.slot(i);
+        if (ring.slot(i) != new_slot) ta.old_slot[ta.no++] = ring.slot(i);
+      }
+      for (int i = 0; i < ta.no; ++i) V.push_back(Sh[ta.old_slot[i]]);
+      for (int i = 0; i < ta.no; ++i) V.push_back(Yh[ta.old_slot[i]]);
       V.push_back(Yh[new_slot]);
       std::vector<double> cross;
-      if ((rc = gram(V, {g, pgv[pcur], Sh[new_slot], Yh[new_slot], PYh[new_slot]}, cross, st))) return rc;
-      const double* a = res_h + 120;
-      sy(new_slot, new_slot) = a[0] * dV;
-      yy(new_slot, new_slot) = a[1] * dV;
-      Qcur = a[2] * dV;
-      gg = a[3] * dV;
-      Sgv[new_slot] = a[4] * dV;
-      Ygv[new_slot] = a[5] * dV;
-      auto X = [&](int row, int col) { return cross[(size_t)row * 5 + col]; };   // cols: g, Pg, s_new, y_new, Py_new
-      for (int i = 0; i < no; ++i) {
-        const int si = old[i];
-        Sgv[si] = X(i, 0);
-        sy(si, new_slot) = X(i, 3);                 // <s_i, y_new>
-        Ygv[si] = X(no + i, 0);
-        YPg[si] = X(no + i, 1);
-        sy(new_slot, si) = X(no + i, 2);            // <s_new, y_i>
-        yy(si, new_slot) = yy(new_slot, si) = X(no + i, 3);
-        ypy(si, new_slot) = ypy(new_slot, si) = X(no + i, 4);
-      }
-      YPg[new_slot] = X(2 * no, 1);
-      ypy(new_slot, new_slot) = X(2 * no, 4);
-      if (!(sy(new_slot, new_slot) > 0)) ring.clear();   // curvature lost to rounding: restart
-      new_slot = -1;
-    }
-    const int kk = ring.count;
-    // --- two-loop recursion on the Gram scalars with H0 = gamma P (P the
-    // kinetic preconditioner):  q = g - sum alpha_j y_j,  r = gamma P q +
-    // sum (alpha_j - beta_j) s_j,  d = -r, where P q = P g - sum alpha_k P y_k
-    // is a combination of stored vectors and <y_i, P q> follows from the
-    // scalars <y_i, P g> and <y_i, P y_k>.
-    std::vector<double> alpha(kk, 0.0), beta(kk, 0.0), rho(kk, 0.0);
-    for (int i = 0; i < kk; ++i) rho[i] = 1.0 / sy(ring.slot(i), ring.slot(i));
-    for (int i = kk - 1; i >= 0; --i) {
-      double sq = Sgv[ring.slot(i)];
-      for (int j = i + 1; j < kk; ++j) sq -= alpha[j] * sy(ring.slot(i), ring.slot(j));
-      alpha[i] = rho[i] * sq;
-    }
-    double gamma = 1.0, t0 = 1.0;
-    if (kk > 0) {
-      const int sl = ring.slot(kk - 1);
-      gamma = sy(sl, sl) / yy(sl, sl);
-    }
-    for (int i = 0; i < kk; ++i) {
-      double ypq = YPg[ring.slot(i)];
-      for (int k = 0; k < kk; ++k) ypq -= alpha[k] * ypy(ring.slot(i), ring.slot(k));
-      double yr = gamma * ypq;
-      for (int j = 0; j < i; ++j) yr += (alpha[j] - beta[j]) * sy(ring.slot(j), ring.slot(i));
-      beta[i] = rho[i] * yr;
-    }
-    double dd = 0, dg = 0, dpsi = 0;
-    // with history, the first trial (t = 1) is launched right behind the
-    // direction pass, its scale formed on the device (res_d[126, 127]); the
-    // host reads the direction's dots and the trial's result in one round trip
-    bool first_ready = false;
-    double first_f = 0, first_slope = 0, first_E[14], first_scale = 0, first_mu = 0;
-    auto direction = [&](int nk) -> int {
-      // d = -gamma P g + gamma sum alpha_k P y_k - sum (alpha_j - beta_j) s_j
+      if ((rc = gram(V, {g, pgv[pcur], Sh[new_slot], Yh[new_slot], PYh[new_slot]}, cross, st, false))) return rc;
+      // two-loop recursion on the device (k_twoloop), then the direction
+      // d = coef[0] P g + sum (coef[1+2j] P y_j + coef[2+2j] s_j)
+      OFDFT_RUN("k_twoloop", st, 0.0, k_twoloop<<<1, 32, 0, st>>>(ta, res_d + 16, res_d + 120, tl_state, res_d + 129));
       VecList<T> vl{};
       vl.nv = 0;
-      vl.v[vl.nv] = pgv[pcur]; vl.c[vl.nv++] = nk > 0 ? -gamma : -1.0;
-      for (int j = 0; j < nk; ++j) {
-        vl.v[vl.nv] = PYh[ring.slot(j)]; vl.c[vl.nv++] = gamma * alpha[j];
-        vl.v[vl.nv] = Sh[ring.slot(j)]; vl.c[vl.nv++] = -(alpha[j] - beta[j]);
+      vl.v[vl.nv++] = pgv[pcur];
+      for (int j = 0; j < ring.count; ++j) {
+        vl.v[vl.nv++] = PYh[ring.slot(j)];
+        vl.v[vl.nv++] = Sh[ring.slot(j)];
       }
-      int e;
-      if (nk == 0) {
-        if ((e = lincomb(vl, d, &dd, &dg, &dpsi, st))) return e;
-        t0 = 0.1 * std::sqrt(Qcur / std::max(dd, 1e-300));   // first step: 10% of |psi|
-        return OFDFT_OK;
-      }
-      TrialScale ts{Qcur, 1.0, Ne, dV, nbar, res_d + 126};
-      if ((e = lincomb(vl, d, nullptr, nullptr, nullptr, st, ts))) return e;
-      if ((e = eval(1, nullptr, psi, d, 1.0, 1.0, 0.0, 0.0, gp, st, false, mu_ref, res_d + 126))) return e;
+      TrialScale ts{0.0, 1.0, Ne, dV, nbar, res_d + 126, &tl_state->Q, &tl_state->kk};
+      if ((rc = lincomb(vl, d, nullptr, nullptr, nullptr, st, ts, tl_state->coef))) return rc;
+      if ((rc = eval(1, nullptr, psi, d, 1.0, 1.0, 0.0, 0.0, gp, st, false, mu_ref, res_d + 126))) return rc;
       ++evals;
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaMemcpyAsync(res_h + 16, res_d + 16, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-      OFDFT_CK(cudaMemcpyAsync(res_h + 126, res_d + 126, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      OFDFT_CK(cudaMemcpyAsync(res_h + 126, res_d + 126, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaStreamSynchronize(st));
+      // k_accept's dots (copied after the accept) are on the host now
+      Qcur = res_h[122] * dV;
+      gg = res_h[123] * dV;
+      gamma = res_h[129];
+      if (res_h[130] == 0.0) ring.clear();   // curvature lost to rounding: history dropped
+      new_slot = -1;
       dd = res_h[16] * dV; dg = res_h[17] * dV; dpsi = res_h[18] * dV;
-      t0 = 1.0;
+      t0 = res_h[128];
       const double sc = res_h[126];
-      finish_eval(1, sc, Qcur + 2.0 * dpsi + dd, dpsi + dd, mu_ref, merged());
+      finish_eval(1, sc, Qcur + 2.0 * t0 * dpsi + t0 * t0 * dd, dpsi + t0 * dd, mu_ref, merged());
+      first_t = t0;
       first_f = res_h[13] > 0 ? NAN : res_h[7];
       first_slope = res_h[11];
       first_scale = sc; first_mu = res_h[9];
       std::memcpy(first_E, res_h, sizeof(first_E));
       first_ready = true;
-      return OFDFT_OK;
-    };
-    if ((rc = direction(kk))) return rc;
-    if (!(dg < 0) && kk > 0) {
+    } else {
+      if ((rc = steepest())) return rc;
+    }
+    if (!(dg < 0) && ring.count > 0) {
       first_ready = false;
       // not a descent direction: drop the history and restart along -P g
       ring.clear();
-      if ((rc = direction(0))) return rc;
+      if ((rc = steepest())) return rc;
     }
     if (!(dg < 0)) break;
     // --- strong-Wolfe line search along d
     double lastScale = 0, lastMu = 0, lastE[14];
     auto phi = [&](double t, double* f, double* slope) -> int {
-      if (first_ready && t == 1.0) {
+      if (first_ready && t == first_t) {
         first_ready = false;
         *f = first_f; *slope = first_slope;
         lastScale = first_scale; lastMu = first_mu;
@@ -1071,11 +1038,12 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     // energy noise: FP64 rounding, or FP32 terms summed in FP64
     const double rel_noise = sizeof(T) == 4 ? 3e-7 : 1e-14;
     rc = line_search(phi, F, dg, t0, o.c1, o.c2, 40, rel_noise, &acc, &lsev);
-    if (rc == OFDFT_ERR_NOT_CONVERGED && kk > 0) {
+    if (rc == OFDFT_ERR_NOT_CONVERGED && ring.count > 0) {
       // failed along the quasi-Newton direction: drop the history and retry once
       // along -P g (scaled as a first step) before giving up
       ring.clear();
-      if ((rc = direction(0))) return rc;
+      first_ready = false;
+      if ((rc = steepest())) return rc;
       if (dg < 0) {
         int lsev2 = 0;
         rc = line_search(phi, F, dg, t0, o.c1, o.c2, 40, rel_noise, &acc, &lsev2);

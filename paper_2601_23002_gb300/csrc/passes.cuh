@@ -194,8 +194,8 @@ template <typename T> struct ProArgs {
   // gradient amplifies that rounding, so in FP32 this lowers the gradient's
   // noise floor several times.
   T psi_shift;
-  // when set, scale = dsc[0] and psi_shift = dsc[1] (a trial scale formed on
-  // the device, see TrialScale)
+  // when set, scale = dsc[0], psi_shift = dsc[1] and t = dsc[2] (a trial
+  // formed on the device, see TrialScale)
   const double* dsc;
 };
 
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
   cp_async_wait<0>();
   __syncthreads();
   // psi_t (or sqrt rho) in place; the raw density stays in dbuf for mode 0
-  const T tstep = a.t;
+  const T tstep = a.dsc ? (T)a.dsc[2] : a.t;
   for (int q = threadIdx.x; q < tot; q += blockDim.x) {
     const T x = psit[q];
     if (a.mode == 0) { dbuf[q] = x; psit[q] = sqrt(fmax(x, (T)0)); }
@@ -541,7 +541,7 @@ template <typename T> struct EpiArgs {
   // P y = P g_new - P g_old)
   const T* pold;
   T* pyout;
-  const double* dsc;     // when set, scale = dsc[0] (a trial scale formed on the device)
+  const double* dsc;     // when set, scale = dsc[0] and t = dsc[2] (a trial formed on the device)
 };
 
 // smem: stg[nact][R][nh] (complex; field f's real rows overwrite its own
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
   const T Te = a.T_e;
   const T cy = a.cy;
   const T alpha = a.alpha, nmin = (T)kNmin;
-  const T tstep = a.t, tscale = a.dsc ? (T)a.dsc[0] : a.scale, muref = a.mu_ref;
+  const T tstep = a.dsc ? (T)a.dsc[2] : a.t, tscale = a.dsc ? (T)a.dsc[0] : a.scale, muref = a.mu_ref;
   AccShort<T> acc[8];
   // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
   const T* pd = pin + (size_t)Rfull * n;

@@ -171,8 +171,131 @@ k_gram(VecList<T> X, int nv, size_t N, double* __restrict__ partial, unsigned in
 // be launched without a host round trip.  out == nullptr: not wanted.
 struct TrialScale {
   double q, t, ne, dv, nbar;
-  double* out;       // out[0] = scale, out[1] = sqrt(nbar / scale)
+  double* out;       // out[0] = scale, out[1] = sqrt(nbar / scale), out[2] = t
+  // when set: q = *qdev, and t = 1 if *kkdev > 0 (a quasi-Newton step), else
+  // the first step 0.1 sqrt(q / <d,d>) (10% of |psi| along -P g)
+  const double* qdev;
+  const int* kkdev;
 };
+
+// L-BFGS history scalars kept on the device, indexed by ring slot (< 8):
+// <s_a, y_b>, <y_a, y_b>, <y_a, P y_b>, and <s, g>, <y, g>, <y, P g> for the
+// current g; Q = int psi^2; the recursion's gamma, pairs used (kk) and the
+// direction's coefficients (P g first, then (P y_j, s_j) in ring order).
+constexpr int kTLMax = 8;
+struct TwoLoopState {
+  double SY[kTLMax * kTLMax], YY[kTLMax * kTLMax], YPY[kTLMax * kTLMax];
+  double Sg[kTLMax], Yg[kTLMax], YPg[kTLMax];
+  double Q, gamma;
+  double coef[1 + 2 * kTLMax];
+  int kk;
+};
+struct TwoLoopArgs {
+  int count;                  // pairs in the ring, the new one included
+  int new_slot;               // slot of the pair accepted last
+  int no;                     // older pairs
+  int old_slot[kTLMax];       // their slots, ring order
+  int ring_slot[kTLMax];      // all slots, ring order (oldest first)
+  double dv;
+};
+
+// One warp, FP64: fold the new pair into the history scalars from
+// acc[0..5] = k_accept's <s,y>, <y,y>, Q, <g,g>, <s,g>, <y,g> and the Gram
+// pass's cross[row * 5 + col], rows [older s, older y, y_new], columns
+// [g, P g, s_new, y_new, P y_new] (raw sums, times dv here); then the two-loop
+// recursion with H0 = gamma P on those scalars:
+//   q = g - sum alpha_j y_j,  d = -(gamma P q + sum (alpha_j - beta_j) s_j),
+//   P q = P g - sum alpha_k P y_k,  <y_i, P q> = <y_i, P g> - sum alpha_k <y_i, P y_k>.
+// A new pair without positive curvature drops the history (kk = 0, d = -P g).
+// The state is staged in shared memory by the whole warp, and the recursion
+// runs with one lane per pair.  res[0] = gamma, res[1] = kk.
+static __global__ void __launch_bounds__(32) k_twoloop(TwoLoopArgs a, const double* __restrict__ cross,
+                                                       const double* __restrict__ acc,
+                                                       TwoLoopState* __restrict__ st, double* __restrict__ res) {
+  constexpr int M2 = kTLMax * kTLMax;
+  __shared__ double sSY[M2], sYY[M2], sYPY[M2], sSg[kTLMax], sYg[kTLMax], sYPg[kTLMax];
+  __shared__ double sX[(2 * kTLMax + 1) * 5], sA[6], srho[kTLMax], scoef[1 + 2 * kTLMax];
+  __shared__ double sgam;
+  __shared__ int skk;
+  const int lane = threadIdx.x;
+  const int no = a.no, ns = a.new_slot;
+  const double dv = a.dv;
+  for (int q = lane; q < M2; q += 32) { sSY[q] = st->SY[q]; sYY[q] = st->YY[q]; sYPY[q] = st->YPY[q]; }
+  if (lane < kTLMax) { sSg[lane] = st->Sg[lane]; sYg[lane] = st->Yg[lane]; sYPg[lane] = st->YPg[lane]; }
+  for (int q = lane; q < (2 * no + 1) * 5; q += 32) sX[q] = cross[q] * dv;
+  if (lane < 6) sA[lane] = acc[lane] * dv;
+  __syncwarp();
+  // the new pair's rows and columns (lane i < no: older pair i; lane 31: own dots)
+  if (lane < no) {
+    const int si = a.old_slot[lane];
+    const int i = lane;
+    sSg[si] = sX[i * 5 + 0];
+    sSY[si * kTLMax + ns] = sX[i * 5 + 3];
+    sYg[si] = sX[(no + i) * 5 + 0];
+    sYPg[si] = sX[(no + i) * 5 + 1];
+    sSY[ns * kTLMax + si] = sX[(no + i) * 5 + 2];
+    sYY[si * kTLMax + ns] = sYY[ns * kTLMax + si] = sX[(no + i) * 5 + 3];
+    sYPY[si * kTLMax + ns] = sYPY[ns * kTLMax + si] = sX[(no + i) * 5 + 4];
+  } else if (lane == 31) {
+    sSY[ns * kTLMax + ns] = sA[0];
+    sYY[ns * kTLMax + ns] = sA[1];
+    sSg[ns] = sA[4];
+    sYg[ns] = sA[5];
+    sYPg[ns] = sX[2 * no * 5 + 1];
+    sYPY[ns * kTLMax + ns] = sX[2 * no * 5 + 4];
+  }
+  __syncwarp();
+  const int kk = sSY[ns * kTLMax + ns] > 0 ? a.count : 0;
+  // reciprocals of the curvatures, one lane each
+  if (lane < kk) { const int sl = a.ring_slot[lane]; srho[lane] = 1.0 / sSY[sl * kTLMax + sl]; }
+  if (lane == 8 && kk > 0) {
+    const int sl = a.ring_slot[kk - 1];
+    sgam = sSY[sl * kTLMax + sl] / sYY[sl * kTLMax + sl];
+  }
+  __syncwarp();
+  // the recursion with lane i holding pair i (ring order): each alpha_j (and
+  // later alpha_j - beta_j) is broadcast as soon as it is final and the other
+  // lanes fold it in, so the dependent chain is ~2 kk steps long
+  const unsigned FULL = 0xffffffffu;
+  const bool mine = lane < kk;
+  const int rl = mine ? a.ring_slot[lane] : 0;
+  const double gamma = kk > 0 ? sgam : 1.0;
+  double sq = mine ? sSg[rl] : 0.0, alpha_l = 0.0;
+  for (int j = kk - 1; j >= 0; --j) {
+    if (lane == j) alpha_l = srho[j] * sq;
+    const double aj = __shfl_sync(FULL, alpha_l, j);
+    if (lane < j) sq -= aj * sSY[rl * kTLMax + a.ring_slot[j]];
+  }
+  // <y_l, P q> = <y_l, P g> - sum_k alpha_k <y_l, P y_k>, independent per lane
+  double ypq = mine ? sYPg[rl] : 0.0;
+  for (int k = 0; k < kk; ++k) {
+    const double ak = __shfl_sync(FULL, alpha_l, k);
+    if (mine) ypq -= ak * sYPY[rl * kTLMax + a.ring_slot[k]];
+  }
+  double yr = gamma * ypq, beta_l = 0.0;
+  for (int i = 0; i < kk; ++i) {
+    if (lane == i) beta_l = srho[i] * yr;
+    const double di = __shfl_sync(FULL, alpha_l - beta_l, i);
+    if (lane > i && mine) yr += di * sSY[a.ring_slot[i] * kTLMax + rl];
+  }
+  if (lane == 0) scoef[0] = kk > 0 ? -gamma : -1.0;
+  if (lane < kTLMax) {
+    scoef[1 + 2 * lane] = mine ? gamma * alpha_l : 0.0;
+    scoef[2 + 2 * lane] = mine ? -(alpha_l - beta_l) : 0.0;
+  }
+  if (lane == 0) { sgam = gamma; skk = kk; }
+  __syncwarp();
+  for (int q = lane; q < M2; q += 32) { st->SY[q] = sSY[q]; st->YY[q] = sYY[q]; st->YPY[q] = sYPY[q]; }
+  if (lane < kTLMax) { st->Sg[lane] = sSg[lane]; st->Yg[lane] = sYg[lane]; st->YPg[lane] = sYPg[lane]; }
+  if (lane < 1 + 2 * kTLMax) st->coef[lane] = scoef[lane];
+  if (lane == 0) {
+    st->Q = sA[2];
+    st->gamma = sgam;
+    st->kk = skk;
+    res[0] = sgam;
+    res[1] = (double)skk;
+  }
+}
 
 // out = sum_{i < nv} c_i X_i, with X_nv = A and X_{nv+1} = B; the last block
 // writes res[0..2] = <out,out>, <out,A>, <out,B> (raw sums, without dV) and,
@@ -180,7 +303,8 @@ struct TrialScale {
 template <typename T>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 k_lincomb(VecList<T> X, int nv, T* __restrict__ out, size_t N, double* __restrict__ partial,
-          unsigned int* __restrict__ counter, double* __restrict__ res, TrialScale ts) {
+          unsigned int* __restrict__ counter, double* __restrict__ res, TrialScale ts,
+          const double* __restrict__ dcoef) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double red[32];
   using V = typename V16<T>::type;
@@ -188,7 +312,7 @@ k_lincomb(VecList<T> X, int nv, T* __restrict__ out, size_t N, double* __restric
   Acc<T> acc[3];
   T c[kMaxLin - 2];
 #pragma unroll
-  for (int i = 0; i < kMaxLin - 2; ++i) c[i] = i < nv ? (T)X.c[i] : (T)0;
+  for (int i = 0; i < kMaxLin - 2; ++i) c[i] = i < nv ? (T)(dcoef ? dcoef[i] : X.c[i]) : (T)0;
   cpa_stream<T, stream_stages(kMaxLin - 1)>(X, nv + 2, N, smem, [&](const V* mine, size_t p) {
     T s[K];
 #pragma unroll
@@ -221,9 +345,13 @@ k_lincomb(VecList<T> X, int nv, T* __restrict__ out, size_t N, double* __restric
       __syncthreads();                   // res[] written by this block's threads
       if (threadIdx.x == 0) {
         const double dd = res[0] * ts.dv, dpsi = res[2] * ts.dv;
-        const double sc = ts.ne / (ts.q + 2.0 * ts.t * dpsi + ts.t * ts.t * dd);
+        const double q = ts.qdev ? *ts.qdev : ts.q;
+        double t = ts.t;
+        if (ts.kkdev && *ts.kkdev == 0) t = 0.1 * sqrt(q / fmax(dd, 1e-300));
+        const double sc = ts.ne / (q + 2.0 * t * dpsi + t * t * dd);
         ts.out[0] = sc;
         ts.out[1] = sqrt(ts.nbar / sc);
+        ts.out[2] = t;
       }
     }
   }
