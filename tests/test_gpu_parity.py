@@ -315,3 +315,31 @@ def test_module_level_minimize_matches_the_plan():
     # a warm start from the converged density stays there
     rho3, res3 = og.minimize(cell, rho=rho, tol_F_per_ion=1e-10, tol_residual=1e-7)
     assert res3["converged"] and abs(res3["F_total"] - res["F_total"]) < 1e-9
+
+
+@pytest.mark.parametrize("n,precision", [(8, "fp64"), (512, "fp32"), (512, "fp64")])
+def test_grid_size_limits_uniform_density(n, precision):
+    # the smallest and largest grids a plan accepts (8^3: a 6-bohr cell of 4
+    # ions; 512^3: 64 ions in a 40-bohr cell, 0.078 bohr spacing): a uniform
+    # density has the oracle's closed-form energies (vW = NL = H = 0; TF, XC
+    # and the local term from nbar alone) and the Ewald energy of the ions
+    from oracle.functional import uniform_free_energy
+    from oracle.cell import ewald_energy
+    from workloads.cells import Cell
+    L, n_ion = (6.0, 4) if n == 8 else (40.0, 64)
+    rng = np.random.default_rng(SEED_BASE + 71 + n)
+    cell = Cell(L=L, n=n, Z=np.ones(n_ion), pos=rng.uniform(0, L, size=(n_ion, 3)), theta=0.8)
+    plan = og.plan_for_cell(cell, precision=precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    nbar = cell.n_electrons / cell.volume
+    rho = torch.full((n ** 3,), nbar, dtype=dt, device="cuda")
+    e = plan.energy_potential(rho)
+    plan.close()
+    ref = uniform_free_energy(cell)
+    ref_ion = ewald_energy(np.asarray(cell.Z, float), cell.pos, cell.L)
+    tol = 1e-9 if precision == "fp64" else 3e-6
+    for key, r in (("F_TF", ref["tf"]), ("E_xc", ref["xc"]), ("E_loc", ref["loc"]), ("E_ion", ref_ion)):
+        assert abs(e[key] - r) <= tol * max(1.0, abs(r)), (key, e[key], r)
+    for key in ("E_vW", "E_H", "E_NL"):
+        assert abs(e[key]) <= tol * max(1.0, abs(ref["tf"])), (key, e[key])
+    assert abs(e["N_e"] - cell.n_electrons) <= tol * cell.n_electrons
