@@ -43,12 +43,14 @@ __device__ __forceinline__ void ip_stage(cplx<T>* __restrict__ a, int n, int Lsu
     if (line_fastest) { t = qdiv(it, lines, Mli); line = it - t * lines; }
     else { line = qdiv(it, per_line, Mpl); t = it - line * per_line; }
     const int b = qdiv(t, m, Mm), j = t - b * m;
-    cplx<T>* p = a + (size_t)line * ld_line + (size_t)(b * Lsub + j) * ld_elem;
-    const size_t st = (size_t)m * ld_elem;
+    // 32-bit offsets: a plane has at most 160 x 161 elements
+    const int base = line * ld_line + (b * Lsub + j) * ld_elem;
+    const int st = m * ld_elem;
     cplx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = p[r * st];
-    if (DIR > 0) {
+    for (int r = 0; r < R; ++r) v[r] = a[base + r * st];
+    // m == 1 (the last forward / first inverse stage): j = 0, every twiddle is 1
+    if (DIR > 0 && m > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         cplx<T> w = tw[j * r * tstep];             // j r < Lsub, so the index is < n
@@ -57,12 +59,12 @@ __device__ __forceinline__ void ip_stage(cplx<T>* __restrict__ a, int n, int Lsu
       }
     }
     Codelet<cplx<T>, R, DIR>::run(v);
-    if (DIR < 0) {
+    if (DIR < 0 && m > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * tstep]);
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) p[r * st] = v[r];
+    for (int r = 0; r < R; ++r) a[base + r * st] = v[r];
   }
 }
 
