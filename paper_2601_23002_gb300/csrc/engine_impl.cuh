@@ -592,11 +592,12 @@ class Engine : public IEngine {
     int rc;
     if ((rc = sum_partials(sgrid, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
-    const int nimg = (int)std::ceil(rcut / L) + 1;
+    const int nimg = (int)std::ceil(rcut / L) + 1;          // raw displacements (forces)
+    const int nimg_mi = (int)std::ceil(rcut / L + 0.5);     // minimum-image displacements (energy)
     ew_eta = eta; ew_rcut = rcut; ew_nimg = nimg;
-    const long ncomb = (long)nion * nion * (2 * nimg + 1) * (2 * nimg + 1) * (2 * nimg + 1);
+    const long ncomb = (long)nion * nion * (2 * nimg_mi + 1) * (2 * nimg_mi + 1) * (2 * nimg_mi + 1);
     const int gb = (int)std::min<long>(std::min<long>(2048, 4L * nsm), (ncomb + 255) / 256);
-    OFDFT_RUN("k_ewald_real", st, (double)nion * 32, k_ewald_real<<<gb, 256, 0, st>>>(pos_d, Z_d, nion, L, eta, rcut, nimg, partials));
+    OFDFT_RUN("k_ewald_real", st, (double)nion * 32, k_ewald_real<<<gb, 256, 0, st>>>(pos_d, Z_d, nion, L, eta, rcut, nimg_mi, partials));
     if ((rc = sum_partials(gb, 1, 1, st))) return rc;
     OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     OFDFT_CK(cudaStreamSynchronize(st));

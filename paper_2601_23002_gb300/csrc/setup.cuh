@@ -149,29 +149,62 @@ __global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __re
 
 // ---------------------------------------------------------------------------
 // Ewald: real-space pair sum (all pairs I, J and lattice images within rcut).
-// One (pair, image) per thread step, so that the FP64 work (the squared
-// distance for every combination, sqrt and erfc inside the cutoff) spreads
-// over the whole GPU instead of one image loop per pair.
-static __global__ void k_ewald_real(const double* __restrict__ pos, const double* __restrict__ Z, int n_ion,
-                             double L, double eta, double rcut, int nimg, double* __restrict__ partial) {
+// Each pair's displacement is taken at minimum image (|d| <= L/2 per axis), so
+// images a with |a| <= nimg = ceil(rcut/L + 1/2) per axis cover every
+// distance below rcut.  A block walks its share of the (pair, image)
+// combinations 256 at a time, compacts the ones inside rcut into shared
+// memory (warp ballots and a block prefix, in combination order) and only
+// then evaluates erfc, on dense warps: the FP64 erfc is by far the costliest
+// step, and fewer than 1% of the combinations are inside.  Fixed order
+// throughout, so the sum is deterministic.
+static __global__ void __launch_bounds__(256) k_ewald_real(const double* __restrict__ pos,
+                                                           const double* __restrict__ Z, int n_ion, double L,
+                                                           double eta, double rcut, int nimg,
+                                                           double* __restrict__ partial) {
   __shared__ double red[32];
-  double acc = 0;
+  __shared__ double sr[256], sz[256];
+  __shared__ int wcount[8], wbase[8], total;
   const int side = 2 * nimg + 1;
   const long nim3 = (long)side * side * side;
   const long tot = (long)n_ion * n_ion * nim3;
+  const long per = (tot + gridDim.x - 1) / gridDim.x;
+  const long q0 = (long)blockIdx.x * per, q1 = min(tot, q0 + per);
   const double rc2 = rcut * rcut;
-  for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (long)gridDim.x * blockDim.x) {
-    const long p = q / nim3;
-    const int im = (int)(q - p * nim3);
-    const int I = (int)(p / n_ion), J = (int)(p % n_ion);
-    const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
-    const double x = pos[I * 3] - pos[J * 3] + a * L, y = pos[I * 3 + 1] - pos[J * 3 + 1] + b * L,
-                 z = pos[I * 3 + 2] - pos[J * 3 + 2] + c * L;
-    const double r2 = x * x + y * y + z * z;
-    if (r2 > 1e-24 && r2 < rc2) {
-      const double r = sqrt(r2);
-      acc += 0.5 * Z[I] * Z[J] * erfc(eta * r) / r;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double acc = 0;
+  for (long base = q0; base < q1; base += blockDim.x) {
+    const long q = base + threadIdx.x;
+    bool inside = false;
+    double r = 0, zz = 0;
+    if (q < q1) {
+      const long p = q / nim3;
+      const int im = (int)(q - p * nim3);
+      const int I = (int)(p / n_ion), J = (int)(p % n_ion);
+      const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
+      double x = pos[I * 3] - pos[J * 3], y = pos[I * 3 + 1] - pos[J * 3 + 1], z = pos[I * 3 + 2] - pos[J * 3 + 2];
+      const double iL = 1.0 / L;     // uniform: folded to one reciprocal per thread
+      x -= L * rint(x * iL); y -= L * rint(y * iL); z -= L * rint(z * iL);
+      x += a * L; y += b * L; z += c * L;
+      const double r2 = x * x + y * y + z * z;
+      inside = r2 > 1e-24 && r2 < rc2;
+      if (inside) { r = sqrt(r2); zz = Z[I] * Z[J]; }
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, inside);
+    if (lane == 0) wcount[wid] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { wbase[w] = s; s += wcount[w]; }
+      total = s;
+    }
+    __syncthreads();
+    if (inside) {
+      const int slot = wbase[wid] + __popc(bal & ((1u << lane) - 1u));
+      sr[slot] = r; sz[slot] = zz;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < total) acc += 0.5 * sz[threadIdx.x] * erfc(eta * sr[threadIdx.x]) / sr[threadIdx.x];
+    __syncthreads();
   }
   double v[1] = {acc}, out[1];
   block_sum<1>(v, red, out);
