@@ -178,12 +178,8 @@ def run_ours(args, rank, world, local):
         return total_ms, evals, iters, last
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_2601_23002_gb300.sharding import max_over_ranks as mor
+        return mor(x, dev)
 
     res = {}
     plan, rho, pos = make("fp32")
@@ -256,8 +252,13 @@ def run_batched(args, dev):
     outside both timed regions."""
     import torch
     import paper_2601_23002_gb300 as og
+    from paper_2601_23002_gb300.sharding import shard, snapshot_cost, max_over_ranks, sum_over_ranks
     from workloads import batch_cells
-    cells = batch_cells(args.batch_count)
+    # several GPUs: each rank takes its cost-balanced share of the snapshots;
+    # throughput = all snapshots / the slowest rank's time
+    rank, world, _ = dist_env()
+    cells_all = batch_cells(args.batch_count)
+    cells = [cells_all[i] for i in shard([snapshot_cost(c.n) for c in cells_all], world, rank)]
     plans = [og.plan_for_cell(c, precision="fp32") for c in cells]
     for p in plans:
         p.autotune()
@@ -267,20 +268,20 @@ def run_batched(args, dev):
     t0 = time.perf_counter()
     seq = [p.minimize(r, start_uniform=True, tol_F_per_ion=TOL_F, tol_residual=TOL_R) for p, r in zip(plans, rhos)]
     torch.cuda.synchronize(dev)
-    t_seq = time.perf_counter() - t0
-    out = {"workload": f"{len(cells)} snapshots, 16-128 ions, Z in {{1,3,4}}, r_s U[1,3], theta U[0.1,2], "
-                       f"grids {sorted(set(c.n for c in cells))}",
-           "sequential_snapshots_per_s": len(cells) / t_seq}
+    t_seq = max_over_ranks(time.perf_counter() - t0, dev)
+    out = {"workload": f"{len(cells_all)} snapshots, 16-128 ions, Z in {{1,3,4}}, r_s U[1,3], theta U[0.1,2], "
+                       f"grids {sorted(set(c.n for c in cells_all))}",
+           "ranks": world, "sequential_snapshots_per_s": len(cells_all) / t_seq}
     for conc in (8, 16, 32):
         t0 = time.perf_counter()
         res = og.minimize_batch(plans, rhos, concurrency=conc, tol_F_per_ion=TOL_F, tol_residual=TOL_R)
         torch.cuda.synchronize(dev)
-        t = time.perf_counter() - t0
-        out[f"batched_c{conc}_snapshots_per_s"] = len(cells) / t
-        out[f"batched_c{conc}_converged"] = sum(r["converged"] for r in res)
+        t = max_over_ranks(time.perf_counter() - t0, dev)
+        out[f"batched_c{conc}_snapshots_per_s"] = len(cells_all) / t
+        out[f"batched_c{conc}_converged"] = int(sum_over_ranks(sum(r["converged"] for r in res), dev))
     out["speedup_best"] = max(v for k, v in out.items() if k.startswith("batched_c") and k.endswith("per_s")) \
         / out["sequential_snapshots_per_s"]
-    out["converged_sequential"] = sum(r["converged"] for r in seq)
+    out["converged_sequential"] = int(sum_over_ranks(sum(r["converged"] for r in seq), dev))
     for p in plans:
         p.close()
     return out
