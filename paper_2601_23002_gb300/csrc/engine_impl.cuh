@@ -592,9 +592,9 @@ class Engine : public IEngine {
     int rc;
     if ((rc = sum_partials(sgrid, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
-    const int nimg = (int)std::ceil(rcut / L) + 1;          // raw displacements (forces)
-    const int nimg_mi = (int)std::ceil(rcut / L + 0.5);     // minimum-image displacements (energy)
-    ew_eta = eta; ew_rcut = rcut; ew_nimg = nimg;
+    // images per axis around minimum-image displacements
+    const int nimg_mi = (int)std::ceil(rcut / L + 0.5);
+    ew_eta = eta; ew_rcut = rcut; ew_nimg = nimg_mi;
     const long ncomb = (long)nion * nion * (2 * nimg_mi + 1) * (2 * nimg_mi + 1) * (2 * nimg_mi + 1);
     const int gb = (int)std::min<long>(std::min<long>(2048, 4L * nsm), (ncomb + 255) / 256);
     OFDFT_RUN("k_ewald_real", st, (double)nion * 32, k_ewald_real<<<gb, 256, 0, st>>>(pos_d, Z_d, nion, L, eta, rcut, nimg_mi, partials));
@@ -955,7 +955,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       if ((rc = precondition(g, pgv[pnew], st, pgv[pcur], PYh[new_slot]))) return rc;
       pcur = pnew;
       // the accepted pair's own dots came from k_accept (res 120..125); one
-      // pass dots [older s, older y, y_new] with [g, P g, s_new, y_new, P y_new]
+      // pass dots [older s, older y, y_new] with [g, P g, y_new, P y_new]
       TwoLoopArgs ta{};
       ta.count = ring.count; ta.new_slot = new_slot; ta.dv = dV;
       std::vector<const T*> V;
@@ -967,7 +967,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
       for (int i = 0; i < ta.no; ++i) V.push_back(Yh[ta.old_slot[i]]);
       V.push_back(Yh[new_slot]);
       std::vector<double> cross;
-      if ((rc = gram(V, {g, pgv[pcur], Sh[new_slot], Yh[new_slot], PYh[new_slot]}, cross, st, false))) return rc;
+      if ((rc = gram(V, {g, pgv[pcur], Yh[new_slot], PYh[new_slot]}, cross, st, false))) return rc;
       // two-loop recursion on the device (k_twoloop), then the direction
       // d = coef[0] P g + sum (coef[1+2j] P y_j + coef[2+2j] s_j)
       OFDFT_RUN("k_twoloop", st, 0.0, k_twoloop<<<1, 32, 0, st>>>(ta, res_d + 16, res_d + 120, tl_state, res_d + 129));

@@ -464,30 +464,61 @@ __global__ void __launch_bounds__(256) k_forces_g(const cplx<T>* __restrict__ qq
   if (threadIdx.x < 3) out[(size_t)I * 3 + threadIdx.x] = -Z[I] * tp * s[threadIdx.x];
 }
 
-// one block per ion: Ewald real-space force added to out[I*3 ..]; FP64
+// one block per ion: Ewald real-space force added to out[I*3 ..]; FP64.  As in
+// k_ewald_real, displacements are taken at minimum image (|a| <= nimg images
+// per axis then cover every distance below rcut) and the in-range (J, image)
+// terms are compacted before their erfc and exp are evaluated.
 static __global__ void __launch_bounds__(256) k_ewald_force_real(const double* __restrict__ pos,
                                                                  const double* __restrict__ Z, int n_ion, double L,
                                                                  double eta, double rcut, int nimg,
                                                                  double* __restrict__ out) {
   __shared__ double red[3 * 32];
+  __shared__ double sx[256], sy[256], sz[256], sq[256];
+  __shared__ int wcount[8], wbase[8], total;
   const int I = blockIdx.x;
   const int side = 2 * nimg + 1;
   const int nim3 = side * side * side;
   const long tot = (long)n_ion * nim3;
   const double rc2 = rcut * rcut;
   const double c2 = 2.0 * eta / 1.7724538509055160273;   // 2 eta / sqrt(pi)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double iL = 1.0 / L;
   double f[3] = {0, 0, 0};
-  for (long q = threadIdx.x; q < tot; q += blockDim.x) {
-    const int J = (int)(q / nim3), im = (int)(q % nim3);
-    const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
-    const double x = pos[I * 3] - pos[J * 3] + a * L, y = pos[I * 3 + 1] - pos[J * 3 + 1] + b * L,
-                 z = pos[I * 3 + 2] - pos[J * 3 + 2] + c * L;
-    const double r2 = x * x + y * y + z * z;
-    if (r2 > 1e-24 && r2 < rc2) {
-      const double r = sqrt(r2);
-      const double s = Z[I] * Z[J] * (erfc(eta * r) / r2 + c2 * exp(-eta * eta * r2) / r) / r;
-      f[0] += s * x; f[1] += s * y; f[2] += s * z;
+  for (long base = 0; base < tot; base += blockDim.x) {
+    const long q = base + threadIdx.x;
+    bool inside = false;
+    double x = 0, y = 0, z = 0, r2 = 0;
+    if (q < tot) {
+      const int J = (int)(q / nim3), im = (int)(q % nim3);
+      const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
+      x = pos[I * 3] - pos[J * 3]; y = pos[I * 3 + 1] - pos[J * 3 + 1]; z = pos[I * 3 + 2] - pos[J * 3 + 2];
+      x -= L * rint(x * iL); y -= L * rint(y * iL); z -= L * rint(z * iL);
+      x += a * L; y += b * L; z += c * L;
+      r2 = x * x + y * y + z * z;
+      inside = r2 > 1e-24 && r2 < rc2;
+      if (inside) r2 = Z[I] * Z[J];     // reused below as the charge product
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, inside);
+    if (lane == 0) wcount[wid] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { wbase[w] = s; s += wcount[w]; }
+      total = s;
+    }
+    __syncthreads();
+    if (inside) {
+      const int slot = wbase[wid] + __popc(bal & ((1u << lane) - 1u));
+      sx[slot] = x; sy[slot] = y; sz[slot] = z; sq[slot] = r2;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < total) {
+      const double dx = sx[threadIdx.x], dy = sy[threadIdx.x], dz = sz[threadIdx.x];
+      const double rr = dx * dx + dy * dy + dz * dz, r = sqrt(rr);
+      const double s = sq[threadIdx.x] * (erfc(eta * r) / rr + c2 * exp(-eta * eta * rr) / r) / r;
+      f[0] += s * dx; f[1] += s * dy; f[2] += s * dz;
+    }
+    __syncthreads();
   }
   double o[3];
   block_sum<3>(f, red, o);

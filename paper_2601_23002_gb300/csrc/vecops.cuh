@@ -201,8 +201,10 @@ struct TwoLoopArgs {
 
 // One warp, FP64: fold the new pair into the history scalars from
 // acc[0..5] = k_accept's <s,y>, <y,y>, Q, <g,g>, <s,g>, <y,g> and the Gram
-// pass's cross[row * 5 + col], rows [older s, older y, y_new], columns
-// [g, P g, s_new, y_new, P y_new] (raw sums, times dv here); then the two-loop
+// pass's cross[row * 4 + col], rows [older s, older y, y_new], columns
+// [g, P g, y_new, P y_new] (raw sums, times dv here).  The recursion reads
+// <s_a, y_b> only for a older than b, <y, y> only on the newest pair, and
+// <y, P y>, <y, P g>, <s, g>; nothing else is kept.  Then the two-loop
 // recursion with H0 = gamma P on those scalars:
 //   q = g - sum alpha_j y_j,  d = -(gamma P q + sum (alpha_j - beta_j) s_j),
 //   P q = P g - sum alpha_k P y_k,  <y_i, P q> = <y_i, P g> - sum alpha_k <y_i, P y_k>.
@@ -214,7 +216,7 @@ static __global__ void __launch_bounds__(32) k_twoloop(TwoLoopArgs a, const doub
                                                        TwoLoopState* __restrict__ st, double* __restrict__ res) {
   constexpr int M2 = kTLMax * kTLMax;
   __shared__ double sSY[M2], sYY[M2], sYPY[M2], sSg[kTLMax], sYg[kTLMax], sYPg[kTLMax];
-  __shared__ double sX[(2 * kTLMax + 1) * 5], sA[6], srho[kTLMax], scoef[1 + 2 * kTLMax];
+  __shared__ double sX[(2 * kTLMax + 1) * 4], sA[6], srho[kTLMax], scoef[1 + 2 * kTLMax];
   __shared__ double sgam;
   __shared__ int skk;
   const int lane = threadIdx.x;
@@ -222,27 +224,25 @@ static __global__ void __launch_bounds__(32) k_twoloop(TwoLoopArgs a, const doub
   const double dv = a.dv;
   for (int q = lane; q < M2; q += 32) { sSY[q] = st->SY[q]; sYY[q] = st->YY[q]; sYPY[q] = st->YPY[q]; }
   if (lane < kTLMax) { sSg[lane] = st->Sg[lane]; sYg[lane] = st->Yg[lane]; sYPg[lane] = st->YPg[lane]; }
-  for (int q = lane; q < (2 * no + 1) * 5; q += 32) sX[q] = cross[q] * dv;
+  for (int q = lane; q < (2 * no + 1) * 4; q += 32) sX[q] = cross[q] * dv;
   if (lane < 6) sA[lane] = acc[lane] * dv;
   __syncwarp();
   // the new pair's rows and columns (lane i < no: older pair i; lane 31: own dots)
   if (lane < no) {
     const int si = a.old_slot[lane];
     const int i = lane;
-    sSg[si] = sX[i * 5 + 0];
-    sSY[si * kTLMax + ns] = sX[i * 5 + 3];
-    sYg[si] = sX[(no + i) * 5 + 0];
-    sYPg[si] = sX[(no + i) * 5 + 1];
-    sSY[ns * kTLMax + si] = sX[(no + i) * 5 + 2];
-    sYY[si * kTLMax + ns] = sYY[ns * kTLMax + si] = sX[(no + i) * 5 + 3];
-    sYPY[si * kTLMax + ns] = sYPY[ns * kTLMax + si] = sX[(no + i) * 5 + 4];
+    sSg[si] = sX[i * 4 + 0];                                   // <s_i, g>
+    sSY[si * kTLMax + ns] = sX[i * 4 + 2];                     // <s_i, y_new>
+    sYg[si] = sX[(no + i) * 4 + 0];                            // <y_i, g>
+    sYPg[si] = sX[(no + i) * 4 + 1];                           // <y_i, P g>
+    sYPY[si * kTLMax + ns] = sYPY[ns * kTLMax + si] = sX[(no + i) * 4 + 3];   // <y_i, P y_new>
   } else if (lane == 31) {
     sSY[ns * kTLMax + ns] = sA[0];
     sYY[ns * kTLMax + ns] = sA[1];
     sSg[ns] = sA[4];
     sYg[ns] = sA[5];
-    sYPg[ns] = sX[2 * no * 5 + 1];
-    sYPY[ns * kTLMax + ns] = sX[2 * no * 5 + 4];
+    sYPg[ns] = sX[2 * no * 4 + 1];
+    sYPY[ns * kTLMax + ns] = sX[2 * no * 4 + 3];
   }
   __syncwarp();
   const int kk = sSY[ns * kTLMax + ns] > 0 ? a.count : 0;
