@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libofdft_gb300.so")
-SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "plane_f32.cu", "plane_f64.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "engine_f32.cu", "engine_f64.cu", "plane_f32.cu", "plane_f64.cu", "plane2_f32.cu",
+           "plane2_f64.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -101,6 +101,11 @@ class Engine : public IEngine {
   size_t smem_pl = 0;
   int* rev_d = nullptr;      // position -> frequency of the in-place transforms
   PlaneKernel<T> plane_kern = nullptr;   // k_plane compiled for this grid's radices
+  // one-field preconditioning pass on two-block clusters (half a plane per
+  // block) when half a plane fits in shared memory
+  bool prec2 = false, prec2_allowed = true;
+  size_t smem_pl2 = 0;
+  PlaneKernel<T> prec2_kern = nullptr;
   C* vloc_pl = nullptr;      // V_loc in plane layout and position order
   C* spec[3] = {nullptr, nullptr, nullptr};
   T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
@@ -163,6 +168,8 @@ class Engine : public IEngine {
     tune.zR = env("OFDFT_ZR");
     const char* pe = std::getenv("OFDFT_PLANE");
     plane_allowed = !(pe && pe[0] == '0');
+    const char* p2 = std::getenv("OFDFT_PREC2");
+    prec2_allowed = !(p2 && p2[0] == '0');
     tune.yJ = env("OFDFT_YJ");
     tune.xJ = env("OFDFT_XJ");
   }
@@ -265,6 +272,8 @@ class Engine : public IEngine {
     smem_pl = std::max(((size_t)n * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int),
                        tree_scratch_bytes<T>(4, kPlaneThreads));
     planes = plane_allowed && smem_pl <= (size_t)225 * 1024;
+    smem_pl2 = ((size_t)(n / 2) * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int);
+    prec2 = plane_allowed && prec2_allowed && smem_pl2 <= (size_t)225 * 1024;
     // streaming vector kernels: a multiple of the SM count (4 resident blocks
     // per SM); the async-copy ring kernels hold 160 KB of shared memory, one
     // block per SM
@@ -297,6 +306,7 @@ class Engine : public IEngine {
     }
     pn.n = n; ph.n = h;
     if (planes) plane_kern = plane_kernel<T>(radix_mask(pn));
+    if (prec2) prec2_kern = plane_prec2_kernel<T>(radix_mask(pn));
     int rc;
     // twiddles
     std::vector<C> twn(n), twh(h);
@@ -317,7 +327,7 @@ class Engine : public IEngine {
       if ((rc = alloc(&spec[f], NH))) return rc;
     if ((rc = alloc(&vloc, NH))) return rc;
     if ((rc = alloc(&Sg, NH))) return rc;
-    if (planes) {
+    if (planes || prec2) {
       // frequency at each position after the in-place forward stages:
       // position p = sum_s k_s m_s (m_s = block length / R_s at stage s)
       // holds frequency sum_s k_s R_1 ... R_(s-1)
@@ -335,7 +345,7 @@ class Engine : public IEngine {
       }
       if ((rc = alloc(&rev_d, n))) return rc;
       OFDFT_CK(cudaMemcpyAsync(rev_d, rev.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-      if ((rc = alloc(&vloc_pl, NH))) return rc;
+      if (planes && (rc = alloc(&vloc_pl, NH))) return rc;
     }
     if ((rc = alloc(&psi, N))) return rc;
     if ((rc = alloc(&d, N))) return rc;
@@ -475,6 +485,7 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
     if ((rc = raise((const void*)k_xpass<T, -1>, smem_xp))) return rc;
     if (planes && (rc = raise((const void*)plane_kern, smem_pl))) return rc;
+    if (prec2 && (rc = raise((const void*)prec2_kern, smem_pl2))) return rc;
     const size_t sring = StreamCfg<T>::ring_bytes(3, 17);   // largest ring any streaming launch uses
     if ((rc = raise((const void*)k_gram<T, 1, 3>, sring))) return rc;
     if ((rc = raise((const void*)k_gram<T, 2, 3>, sring))) return rc;
@@ -662,7 +673,7 @@ class Engine : public IEngine {
   // plain vector with the G-space factor p(m^2) (GArgs::prec, EpiArgs mode 3)
   int precondition(const T* in, T* out, cudaStream_t st, const T* pold = nullptr, T* pyout = nullptr) {
     Spectra<T> sp{};
-    sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = planes ? 1 : 0;
+    sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = (planes || prec2) ? 1 : 0;
     ProArgs<T> pa{1, nullptr, in, nullptr, (T)0, (T)1, (T)cs.alpha, (T)0};
     const double tp = 2.0 * kPi / L;
     using TV = typename TreeVal<T>::type;
@@ -671,7 +682,10 @@ class Engine : public IEngine {
                 precT};
     const double fb = 2.0 * NH * sizeof(C);
     OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
-    if (planes) {
+    if (prec2) {
+      // one field: two blocks (a cluster) per kz plane
+      OFDFT_RUN("k_plane_prec2", st, fb, prec2_kern<<<dim3(2 * nh), kPlaneThreads, smem_pl2, st>>>(sp, ga, pn, rev_d, tw_n));
+    } else if (planes) {
       OFDFT_RUN("k_plane", st, fb, plane_kern<<<dim3(nh, 1), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
     } else {
       OFDFT_RUN("k_ypass", st, fb, k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));

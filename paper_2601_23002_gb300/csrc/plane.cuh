@@ -20,6 +20,7 @@
 // Shared memory: plane[n][n + 1] (odd row pitch: row-parallel and
 // column-parallel access are both free of bank conflicts) | tw[n] | rev[n].
 #pragma once
+#include <cooperative_groups.h>
 #include "passes.cuh"
 
 namespace ofdft {
@@ -122,6 +123,88 @@ __device__ __forceinline__ void ip_fft_axis(cplx<T>* a, const FftPlan1& p, int l
   }
 }
 
+// As ip_fft_axis, over `lines` lines (a part of the plane).
+template <typename T, int DIR, unsigned MASK>
+__device__ __forceinline__ void ip_fft_axis_lines(cplx<T>* a, const FftPlan1& p, int ld_elem, int ld_line,
+                                                  bool rows, int lines, const cplx<T>* tw) {
+  const int n = p.n;
+  int Ls[8];
+  int Lsub = n;
+  for (int s = 0; s < p.npass; ++s) { Ls[s] = Lsub; Lsub /= p.radix[s]; }
+  for (int q = 0; q < p.npass; ++q) {
+    const int s = DIR < 0 ? q : p.npass - 1 - q;
+    const int R = p.radix[s];
+    const bool line_fastest = !rows || Ls[s] / R < 32;
+    ip_stage_any<T, DIR, MASK>(R, a, n, Ls[s], ld_elem, ld_line, lines, line_fastest, tw);
+    __syncthreads();
+  }
+}
+
+// One in-place stage (as ip_stage) along columns of a plane whose rows are
+// split between the two blocks of a cluster: row r lives in part[r / half] at
+// offset (r % half) * pitch, part 0 = p0, part 1 = p1.  Transforms the ncols
+// columns col0 .. col0+ncols-1.
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void ip_stage_cols2(cplx<T>* p0, cplx<T>* p1, int half, int pitch, int n, int Lsub,
+                                               int col0, int ncols, const cplx<T>* __restrict__ tw) {
+  const int m = Lsub / R;
+  const int items = (n / R) * ncols;
+  const int tstep = n / Lsub;
+  const unsigned Mm = qmagic(m), Mc = qmagic(ncols);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int t = qdiv(it, ncols, Mc), col = col0 + (it - t * ncols);
+    const int b = qdiv(t, m, Mm), j = t - b * m;
+    const int row0 = b * Lsub + j;
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = row0 + r * m;
+      const bool hi = row >= half;
+      v[r] = (hi ? p1 : p0)[(row - (hi ? half : 0)) * pitch + col];
+    }
+    if (DIR > 0 && m > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cplx<T> w = tw[j * r * tstep];
+        w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    Codelet<cplx<T>, R, DIR>::run(v);
+    if (DIR < 0 && m > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * tstep]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = row0 + r * m;
+      const bool hi = row >= half;
+      (hi ? p1 : p0)[(row - (hi ? half : 0)) * pitch + col] = v[r];
+    }
+  }
+}
+
+template <typename T, int DIR, unsigned MASK>
+__device__ __forceinline__ void ip_stage_cols2_any(int R, cplx<T>* p0, cplx<T>* p1, int half, int pitch, int n,
+                                                   int Lsub, int col0, int ncols, const cplx<T>* tw) {
+#define OFDFT_IP2_CASE(RR)                                                                \
+  if constexpr (((MASK >> RR) & 1u) != 0) {                                              \
+    if (R == RR) { ip_stage_cols2<T, RR, DIR>(p0, p1, half, pitch, n, Lsub, col0, ncols, tw); return; } \
+  }
+  OFDFT_IP2_CASE(16)
+  OFDFT_IP2_CASE(8)
+  OFDFT_IP2_CASE(12)
+  OFDFT_IP2_CASE(10)
+  OFDFT_IP2_CASE(9)
+  OFDFT_IP2_CASE(6)
+  OFDFT_IP2_CASE(5)
+  OFDFT_IP2_CASE(4)
+  OFDFT_IP2_CASE(3)
+  OFDFT_IP2_CASE(2)
+  OFDFT_IP2_CASE(15)
+#undef OFDFT_IP2_CASE
+}
+
 constexpr int kPlaneThreads = 512;
 
 // grid.x = kz plane (n/2 + 1), grid.y = active field.  Spectra in plane
@@ -215,12 +298,85 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
   block_sum_tree_raw<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
 }
 
+// The one-field preconditioning pass (out = IFFT[p(G) FFT(in)], GArgs::prec)
+// on one kz plane per cluster of two blocks: block `rank` holds rows
+// rank*n/2 .. rank*n/2 + n/2 - 1 of the plane (half the shared memory of
+// k_plane); the transforms along rows are local, those along columns split the
+// columns between the pair and reach the partner's rows through distributed
+// shared memory, with a cluster barrier after every stage.  With one field the
+// plain plane pass occupies only n/2 + 1 SMs; this uses twice as many, each
+// with half the work.  grid.x = 2 (n/2 + 1).
+template <typename T, unsigned MASK>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneThreads, 1)
+k_plane_prec2(Spectra<T> sp, GArgs<T> g, FftPlan1 pn, const int* __restrict__ rev_g,
+              const cplx<T>* __restrict__ tw_g) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = pn.n, pitch = n + 1, half = n / 2, nn = n * n;
+  const int rank = (int)cl.block_rank();
+  cplx<T>* a = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tw = a + (size_t)half * pitch;
+  int* rev = reinterpret_cast<int*>(tw + n);
+  cplx<T>* const p0 = rank == 0 ? a : cl.map_shared_rank(a, 0);   // rows 0 .. n/2 - 1
+  cplx<T>* const p1 = rank == 1 ? a : cl.map_shared_rank(a, 1);   // rows n/2 .. n - 1
+  const int kz = blockIdx.x >> 1;
+  const int fid = sp.idx[0];
+  cplx<T>* gpl = sp.s[fid] + (size_t)kz * nn + (size_t)rank * half * n;   // this block's rows
+  const unsigned Mn = qmagic(n);
+  for (int q = threadIdx.x; q < half * n; q += blockDim.x) {
+    const int r = qdiv(q, n, Mn), c = q - r * n;
+    cp_async_c(a + r * pitch + c, gpl + q, true);
+  }
+  cp_async_commit();
+  for (int q = threadIdx.x; q < n; q += blockDim.x) { tw[q] = tw_g[q]; rev[q] = rev_g[q]; }
+  cp_async_wait<0>();
+  __syncthreads();
+  ip_fft_axis_lines<T, -1, MASK>(a, pn, 1, pitch, true, half, tw);   // along ky, own rows
+  cl.sync();
+  int Ls[8];
+  {
+    int Lsub = n;
+    for (int s = 0; s < pn.npass; ++s) { Ls[s] = Lsub; Lsub /= pn.radix[s]; }
+  }
+  for (int q = 0; q < pn.npass; ++q) {                                 // along kx, half the columns
+    ip_stage_cols2_any<T, -1, MASK>(pn.radix[q], p0, p1, half, pitch, n, Ls[q], rank * half, half, tw);
+    cl.sync();
+  }
+  // p(G) f~(G) on own rows
+  const T invN = g.invN;
+  for (int q = threadIdx.x; q < half * n; q += blockDim.x) {
+    const int r = qdiv(q, n, Mn), py = q - r * n;
+    const int px = rank * half + r;
+    const int kx = rev[px], ky = rev[py];
+    const int mx = kx <= n / 2 - 1 ? kx : kx - n;
+    const int my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int m2 = mx * mx + my * my + kz * kz;
+    cplx<T>* cell = a + r * pitch + py;
+    const cplx<T> v = *cell;
+    const T pg = g.prec[m2];
+    *cell = mk<T>(pg * v.x * invN, pg * v.y * invN);
+  }
+  cl.sync();
+  for (int q = 0; q < pn.npass; ++q) {                                 // inverse along kx
+    const int st = pn.npass - 1 - q;
+    ip_stage_cols2_any<T, 1, MASK>(pn.radix[st], p0, p1, half, pitch, n, Ls[st], rank * half, half, tw);
+    cl.sync();                                                         // (last: no remote access after)
+  }
+  ip_fft_axis_lines<T, 1, MASK>(a, pn, 1, pitch, true, half, tw);    // inverse along ky, own rows
+  for (int q = threadIdx.x; q < half * n; q += blockDim.x) {
+    const int r = qdiv(q, n, Mn), c = q - r * n;
+    gpl[q] = a[r * pitch + c];
+  }
+}
+
 // The plane kernel compiled for a plan's radices (instantiated in
 // plane_f32.cu / plane_f64.cu for the radix sets of the supported grids; any
 // other set gets the kernel with every radix).
 template <typename T>
 using PlaneKernel = void (*)(Spectra<T>, GArgs<T>, FftPlan1, const int*, const cplx<T>*);
 template <typename T> PlaneKernel<T> plane_kernel(unsigned mask);
+template <typename T> PlaneKernel<T> plane_prec2_kernel(unsigned mask);
 
 // One-time reorder of V_loc from the tiled layout [kx][ky][kz] into plane
 // layout and position order: dst[(kz n + px) n + py] = src[(rev[px] n + rev[py]) nh + kz].

@@ -343,3 +343,28 @@ def test_grid_size_limits_uniform_density(n, precision):
     for key in ("E_vW", "E_H", "E_NL"):
         assert abs(e[key]) <= tol * max(1.0, abs(ref["tf"])), (key, e[key])
     assert abs(e["N_e"] - cell.n_electrons) <= tol * cell.n_electrons
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cluster_preconditioning_pass_reaches_the_same_minimum(precision, monkeypatch):
+    # the one-field preconditioning pass runs on two-block clusters (half a
+    # kz plane per block, columns through distributed shared memory) by
+    # default; OFDFT_PREC2=0 runs it on one block per plane.  P is the same
+    # linear operator either way, so both minimisations reach the same minimum
+    cell = CASES[4][1]()
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    tol = dict(tol_F_per_ion=1e-10, tol_residual=1e-7) if precision == "fp64" else {}
+    out = []
+    for env in (None, "0"):
+        if env is not None:
+            monkeypatch.setenv("OFDFT_PREC2", env)
+        plan = og.plan_for_cell(cell, precision=precision)
+        rho = torch.empty(cell.n ** 3, dtype=dt, device="cuda")
+        r = plan.minimize(rho, start_uniform=True, **tol)
+        plan.close()
+        assert r["converged"], r
+        out.append((r, rho.double().cpu().numpy()))
+    (r1, n1), (r2, n2) = out
+    tolF = 1e-9 if precision == "fp64" else 1e-6
+    assert abs(r1["F_total"] - r2["F_total"]) / cell.n_ion < tolF
+    assert np.linalg.norm(n1 - n2) / np.linalg.norm(n2) < (1e-6 if precision == "fp64" else 1e-4)
