@@ -354,8 +354,9 @@ k_plane_prec2(Spectra<T> sp, GArgs<T> g, FftPlan1 pn, const int* __restrict__ re
     const int m2 = mx * mx + my * my + kz * kz;
     cplx<T>* cell = a + r * pitch + py;
     const cplx<T> v = *cell;
+    const T vr = v.x * invN, vi = v.y * invN;   // as k_plane: the same bits
     const T pg = g.prec[m2];
-    *cell = mk<T>(pg * v.x * invN, pg * v.y * invN);
+    *cell = mk<T>(pg * vr, pg * vi);
   }
   cl.sync();
   for (int q = 0; q < pn.npass; ++q) {                                 // inverse along kx

@@ -354,6 +354,7 @@ def test_cluster_preconditioning_pass_reaches_the_same_minimum(precision, monkey
     cell = CASES[4][1]()
     dt = torch.float32 if precision == "fp32" else torch.float64
     tol = dict(tol_F_per_ion=1e-10, tol_residual=1e-7) if precision == "fp64" else {}
+    # (FP64 on this 50^3 grid: a whole plane fits as well, so both are plane passes)
     out = []
     for env in (None, "0"):
         if env is not None:
@@ -365,6 +366,6 @@ def test_cluster_preconditioning_pass_reaches_the_same_minimum(precision, monkey
         assert r["converged"], r
         out.append((r, rho.double().cpu().numpy()))
     (r1, n1), (r2, n2) = out
-    tolF = 1e-9 if precision == "fp64" else 1e-6
-    assert abs(r1["F_total"] - r2["F_total"]) / cell.n_ion < tolF
-    assert np.linalg.norm(n1 - n2) / np.linalg.norm(n2) < (1e-6 if precision == "fp64" else 1e-4)
+    # same stages, same twiddles, same G-space rounding: the same bits
+    assert r1["F_total"] == r2["F_total"] and r1["evaluations"] == r2["evaluations"]
+    assert np.array_equal(n1, n2)
