@@ -272,8 +272,12 @@ class Engine : public IEngine {
     smem_pl = std::max(((size_t)n * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int),
                        tree_scratch_bytes<T>(4, kPlaneThreads));
     planes = plane_allowed && smem_pl <= (size_t)225 * 1024;
+    // clusters only for large grids: below n = 112 the snapshots that are
+    // solved side by side (batched, served) fill the GPU anyway, and a
+    // cluster launch waits for pairs of free SMs (64 cells of 48^3-96^3:
+    // 712 -> 669 snapshots/s with clusters)
     smem_pl2 = ((size_t)(n / 2) * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int);
-    prec2 = plane_allowed && prec2_allowed && smem_pl2 <= (size_t)225 * 1024;
+    prec2 = plane_allowed && prec2_allowed && n >= 112 && smem_pl2 <= (size_t)225 * 1024;
     // streaming vector kernels: a multiple of the SM count (4 resident blocks
     // per SM); the async-copy ring kernels hold 160 KB of shared memory, one
     // block per SM

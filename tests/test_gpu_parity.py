@@ -347,6 +347,63 @@ def test_grid_size_limits_uniform_density(n, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_cluster_preconditioning_pass_reaches_the_same_minimum(precision, monkeypatch):
+    # on grids from 112 up the one-field preconditioning pass runs on
+    # two-block clusters (half a kz plane per block, columns through
+    # distributed shared memory); OFDFT_PREC2=0 runs it on one block per plane
+    # (FP32 128^3: identical arithmetic, the same bits) or, where a whole FP64
+    # plane does not fit, on the tiled chain (the same minimum)
+    cell = config_cell(2)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    tol = dict(tol_F_per_ion=1e-10, tol_residual=1e-7) if precision == "fp64" else {}
+    out = []
+    for env in (None, "0"):
+        if env is not None:
+            monkeypatch.setenv("OFDFT_PREC2", env)
+        plan = og.plan_for_cell(cell, precision=precision)
+        rho = torch.empty(cell.n ** 3, dtype=dt, device="cuda")
+        r = plan.minimize(rho, start_uniform=True, **tol)
+        plan.close()
+        assert r["converged"], r
+        out.append((r, rho.double().cpu().numpy()))
+    (r1, n1), (r2, n2) = out
+    if precision == "fp32":
+        assert r1["F_total"] == r2["F_total"] and r1["evaluations"] == r2["evaluations"]
+        assert np.array_equal(n1, n2)
+    else:
+        assert abs(r1["F_total"] - r2["F_total"]) / cell.n_ion < 1e-9
+        assert np.linalg.norm(n1 - n2) / np.linalg.norm(n2) < 1e-6
+
+
+@pytest.mark.parametrize("n,precision", [(8, "fp64"), (512, "fp32"), (512, "fp64")])
+def test_grid_size_limits_uniform_density(n, precision):
+    # the smallest and largest grids a plan accepts (8^3: a 6-bohr cell of 4
+    # ions; 512^3: 64 ions in a 40-bohr cell, 0.078 bohr spacing): a uniform
+    # density has the oracle's closed-form energies (vW = NL = H = 0; TF, XC
+    # and the local term from nbar alone) and the Ewald energy of the ions
+    from oracle.functional import uniform_free_energy
+    from oracle.cell import ewald_energy
+    from workloads.cells import Cell
+    L, n_ion = (6.0, 4) if n == 8 else (40.0, 64)
+    rng = np.random.default_rng(SEED_BASE + 71 + n)
+    cell = Cell(L=L, n=n, Z=np.ones(n_ion), pos=rng.uniform(0, L, size=(n_ion, 3)), theta=0.8)
+    plan = og.plan_for_cell(cell, precision=precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    nbar = cell.n_electrons / cell.volume
+    rho = torch.full((n ** 3,), nbar, dtype=dt, device="cuda")
+    e = plan.energy_potential(rho)
+    plan.close()
+    ref = uniform_free_energy(cell)
+    ref_ion = ewald_energy(np.asarray(cell.Z, float), cell.pos, cell.L)
+    tol = 1e-9 if precision == "fp64" else 3e-6
+    for key, r in (("F_TF", ref["tf"]), ("E_xc", ref["xc"]), ("E_loc", ref["loc"]), ("E_ion", ref_ion)):
+        assert abs(e[key] - r) <= tol * max(1.0, abs(r)), (key, e[key], r)
+    for key in ("E_vW", "E_H", "E_NL"):
+        assert abs(e[key]) <= tol * max(1.0, abs(ref["tf"])), (key, e[key])
+    assert abs(e["N_e"] - cell.n_electrons) <= tol * cell.n_electrons
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cluster_preconditioning_pass_reaches_the_same_minimum(precision, monkeypatch):
     # the one-field preconditioning pass runs on two-block clusters (half a
     # kz plane per block, columns through distributed shared memory) by
     # default; OFDFT_PREC2=0 runs it on one block per plane.  P is the same
