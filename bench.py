@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -83,7 +84,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples; OFDFT_CLOCKS_DIR keeps them somewhere chosen (default: the temp directory)
+        d = os.environ.get("OFDFT_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"ofdft_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
