@@ -18,12 +18,15 @@ the paper names, that it follows):
 * ``functional``   F_s[n;T] = TF + vW + NL (Eq. 1) plus Hartree, local PP and
                    XC; energy and potential.
 * ``minimize``     L-BFGS on sqrt(n) at fixed electron number.
-* ``sei``          electron-ion static structure factor on |q| shells
-                   (Methods, static structure factors).
+* ``sei``          electron-ion and ion-ion static structure factors on |q|
+                   shells, the direct-sum form for large cells, trajectory
+                   averages (Methods, static structure factors).
 * ``forces``       Hellmann-Feynman forces on the ions (Methods, molecular
                    dynamics).
 * ``pressure``     P = -dF/dOmega under a homogeneous dilation (Results,
                    Table 1 and Fig. 3 report pressures).
+* ``md``           Born-Oppenheimer ion dynamics, velocity Verlet with a
+                   Nose-Hoover thermostat (Methods, molecular dynamics).
 
 Parity status: every function is pinned by the tests in ``tests/test_oracle_*``
 against closed forms, library routines or brute force, except the end-to-end
