@@ -50,6 +50,26 @@ bool factor_radices(int n, int* radix, int* npass) {
   return false;
 }
 
+bool factor_radices_balanced(int n, int* radix, int* npass) {
+  static const int cand[] = {16, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  int first[8], np = 0;
+  if (!factor_radices(n, first, &np)) return false;
+  // among the factorisations with the fewest passes, the smallest largest radix
+  int best[8], bestmax = 1 << 30, fac[8];
+  auto dfs = [&](auto&& self, int rem, int depth, int mx) -> void {
+    if (depth == np) {
+      if (rem == 1 && mx < bestmax) { bestmax = mx; for (int i = 0; i < np; ++i) best[i] = fac[i]; }
+      return;
+    }
+    for (int c : cand)
+      if (rem % c == 0) { fac[depth] = c; self(self, rem / c, depth + 1, mx > c ? mx : c); }
+  };
+  dfs(dfs, n, 0, 0);
+  *npass = np;
+  for (int i = 0; i < np; ++i) radix[i] = best[i];
+  return true;
+}
+
 }  // namespace ofdft
 
 using namespace ofdft;

@@ -51,5 +51,8 @@ void set_error(const std::string& msg);
 
 // 1-D FFT factorisation into supported radices; false if n is not supported
 bool factor_radices(int n, int* radix, int* npass);
+// the same number of passes, with the smallest largest radix (the z passes'
+// half-length transforms: a block's 16 rows give more butterflies per stage)
+bool factor_radices_balanced(int n, int* radix, int* npass);
 
 }  // namespace ofdft
