@@ -78,6 +78,7 @@ struct ofdft_plan {
   IEngine* eng;
   int precision;
   int device;
+  int n_ion;
 };
 
 static bool smooth235(int k) {
@@ -151,6 +152,7 @@ int ofdft_plan_create(const ofdft_cell* cell, const ofdft_opts* opts, void* stre
   ofdft_plan* p = new (std::nothrow) ofdft_plan;
   if (!p) { set_error("host allocation failed"); return OFDFT_ERR_OOM; }
   p->precision = opts->precision;
+  p->n_ion = cell->n_ion;
   cudaGetDevice(&p->device);
   CellSpec s = spec_of(cell, opts);
   p->eng = opts->precision == OFDFT_FP32 ? make_engine_f32(s, 8) : make_engine_f64(s, 8);
@@ -221,6 +223,20 @@ int ofdft_md_run(ofdft_plan* plan, void* rho_io, int start_uniform, double* pos_
   if (!plan || !rho_io || !pos_io || !vel_io || !mass || !o || !th_io) { set_error("NULL argument"); return OFDFT_ERR_INVALID; }
   if (n_steps < 0 || !(o->dt > 0)) { set_error("ofdft_md_run: n_steps >= 0 and dt > 0 required"); return OFDFT_ERR_INVALID; }
   if (o->n_shells > 0 && (!q_out || !sei_sum || !sii_sum)) { set_error("ofdft_md_run: shell outputs required"); return OFDFT_ERR_INVALID; }
+  if (!std::isfinite(o->dt) || !std::isfinite(o->T_ion) || (o->T_ion > 0 && !(o->tau > 0 && std::isfinite(o->tau)))) {
+    set_error("ofdft_md_run: dt, T_ion must be finite; a thermostat (T_ion > 0) needs a finite tau > 0");
+    return OFDFT_ERR_INVALID;
+  }
+  {
+    const int ni = plan->n_ion;
+    for (int i = 0; i < ni; ++i)
+      if (!(mass[i] > 0) || !std::isfinite(mass[i])) { set_error("ofdft_md_run: masses must be finite and > 0"); return OFDFT_ERR_INVALID; }
+    for (int c = 0; c < 3 * ni; ++c)
+      if (!std::isfinite(pos_io[c]) || !std::isfinite(vel_io[c])) {
+        set_error("ofdft_md_run: positions and velocities must be finite");
+        return OFDFT_ERR_INVALID;
+      }
+  }
   const ofdft_min_opts& m = o->min;
   if (m.m < 1 || m.m > 8 || m.max_iter < 1 || !(m.c1 > 0) || !(m.c2 > m.c1) || !(m.c2 < 1)) {
     set_error("bad minimiser options (m in 1..8, max_iter >= 1, 0 < c1 < c2 < 1)");
