@@ -95,6 +95,14 @@ def test_md_reports_a_failed_step():
         plan.md_run(rho, cell.pos, np.zeros((4, 3)), mass, 3, 4.0, start_uniform=True, max_iter=1)
     with pytest.raises(og.OfdftError):
         plan.md_run(rho, cell.pos, np.zeros((4, 3)), mass, 3, -1.0, start_uniform=True)
+    bad = mass.copy()
+    bad[2] = 0.0
+    with pytest.raises(og.OfdftError):
+        plan.md_run(rho, cell.pos, np.zeros((4, 3)), bad, 3, 4.0, start_uniform=True)
+    with pytest.raises(og.OfdftError):
+        plan.md_run(rho, cell.pos, np.full((4, 3), np.nan), mass, 3, 4.0, start_uniform=True)
+    with pytest.raises(og.OfdftError):
+        plan.md_run(rho, cell.pos, np.zeros((4, 3)), mass, 3, 4.0, T_ion=0.1, tau=0.0, start_uniform=True)
     plan.close()
 
 
