@@ -94,6 +94,7 @@ class Engine : public IEngine {
   T* Kt = nullptr;
   C* vloc = nullptr;
   C* Sg = nullptr;
+  C* SZg = nullptr;          // S_Z(G) = sum_I Z_I exp(-i G.R_I), tiled layout (forces)
   // plane path (fused x-y-G-space pass; spectra in plane layout) when a kz
   // plane fits in shared memory
   bool plane_allowed = true;
@@ -350,6 +351,7 @@ class Engine : public IEngine {
       if ((rc = alloc(&spec[f], NH))) return rc;
     if ((rc = alloc(&vloc, NH))) return rc;
     if ((rc = alloc(&Sg, NH))) return rc;
+    if ((rc = alloc(&SZg, NH))) return rc;
     if (planes || prec2) {
       // frequency at each position after the in-place forward stages:
       // position p = sum_s k_s m_s (m_s = block length / R_s at stage s)
@@ -617,12 +619,13 @@ class Engine : public IEngine {
     if (mlim >= 0) {
       OFDFT_CK(cudaMemsetAsync(Sg, 0, NH * sizeof(C), st));
       OFDFT_CK(cudaMemsetAsync(vloc, 0, NH * sizeof(C), st));
+      OFDFT_CK(cudaMemsetAsync(SZg, 0, NH * sizeof(C), st));
     }
     // ions per shared-memory chunk: staged kz phases within 40 KB
     const int sch = std::max(1, std::min(64, (int)(40960 / ((size_t)nh * sizeof(C)))));
     const size_t ssm = (size_t)sch * nh * sizeof(C) + (size_t)kStructRows * sch * sizeof(C) + (size_t)sch * sizeof(T);
     const int sgrid = (nrows + kStructRows - 1) / kStructRows;
-    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, partials));
+    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, SZg, partials));
     int rc;
     if ((rc = sum_partials(sgrid, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
@@ -1280,7 +1283,7 @@ int Engine<T>::forces(const void* rho, double* f_out_h, void* stream_) {
   OFDFT_RUN("k_phases_t", st, (double)tot * (16 + sizeof(C)), k_phases_t<T><<<std::min(4096, (tot + 255) / 256), 256, 0, st>>>(phases, f_pt, tot));
   if (f_ng > 0) {
     const int gq = std::min(4 * nsm, (f_ng + 127) / 128);
-    OFDFT_RUN("k_forces_q", st, (double)f_ng * (sizeof(C) + 32 + sizeof(C)), k_forces_q<T><<<gq, 128, 0, st>>>(spec[0], f_gl, f_gf, f_ng, phases, Z_d, nion, n, 1.0 / (double)N, f_qq));
+    OFDFT_RUN("k_forces_q", st, (double)f_ng * (3 * sizeof(C) + 32), k_forces_q<T><<<gq, 128, 0, st>>>(spec[0], f_gl, f_gf, f_ng, SZg, n, 1.0 / (double)N, f_qq));
     OFDFT_RUN("k_forces_g", st, (double)nion * f_ng * (sizeof(C) + 16), k_forces_g<T><<<nion, 256, 0, st>>>(f_qq, f_gl, f_ng, f_pt, Z_d, n, tp, f_out));
   } else {
     OFDFT_CK(cudaMemsetAsync(f_out, 0, (size_t)nion * 3 * sizeof(double), st));

@@ -39,6 +39,7 @@ static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n
 //   sf_tab[m^2] = (v~(G)/Omega per unit charge, (2 pi/Omega) exp(-G^2/(4 eta^2))/G^2),
 // the second 0 at m^2 = 0: both depend on |G| only and are tabulated once per
 // plan in FP64, so no exponential is evaluated here.
+// S_Z itself is kept as well (SZ_out), for the forces.
 // Shared memory: ez[ch][nh] | xy[kStructRows][ch] (complex) | zz[ch] (T).
 constexpr int kStructRows = 8;
 constexpr int kStructMaxKJ = 9;     // kz per lane: nh <= 32 * 9
@@ -50,6 +51,7 @@ __global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __re
                                                              double g2max, int full, int mlim, int ch,
                                                              cplx<T>* __restrict__ S_out,
                                                              cplx<T>* __restrict__ vloc,
+                                                             cplx<T>* __restrict__ SZ_out,
                                                              double* __restrict__ ew_partial) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
@@ -132,10 +134,12 @@ __global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __re
       if (skip) {
         if (S_out) S_out[rowoff + kz] = mk<T>(0, 0);
         vloc[rowoff + kz] = mk<T>(0, 0);
+        SZ_out[rowoff + kz] = mk<T>(0, 0);
         continue;
       }
       const int m2 = mx * mx + my * my + kz * kz;
       if (S_out) S_out[rowoff + kz] = mk<T>(sr[j], si[j]);
+      SZ_out[rowoff + kz] = mk<T>(zr[j], zi[j]);
       const double2 f = sf_tab[m2];
       vloc[rowoff + kz] = mk<T>((T)(f.x * (double)zr[j]), (T)(f.x * (double)zi[j]));
       const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
@@ -402,28 +406,21 @@ namespace ofdft {
 // The G list and the signed m of each index are those of k_struct, so the
 // forces are the exact derivative of the energy the evaluation computes.
 
-// one thread per listed G: qq(G); FP64 (a sum over all ions per G)
+// one thread per listed G: qq(G) = w conj(vfac n~ + efac S_Z), with S_Z(G) as
+// k_struct formed it (plan precision)
 template <typename T>
 __global__ void k_forces_q(const cplx<T>* __restrict__ nt, const int4* __restrict__ gl,
-                           const double2* __restrict__ gf, int ng, const double2* __restrict__ ph,
-                           const double* __restrict__ Z, int n_ion, int n, double invN,
-                           cplx<T>* __restrict__ qq) {
+                           const double2* __restrict__ gf, int ng, const cplx<T>* __restrict__ SZ, int n,
+                           double invN, cplx<T>* __restrict__ qq) {
   const int nh = n / 2 + 1;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
     const int4 e = gl[g];
-    const cplx<T> v = nt[((size_t)e.x * n + e.y) * nh + e.z];
-    double ar = 0, ai = 0;
-    for (int J = 0; J < n_ion; ++J) {
-      const double2 px = ph[((size_t)J * 3 + 0) * n + e.x];
-      const double2 py = ph[((size_t)J * 3 + 1) * n + e.y];
-      const double2 pz = ph[((size_t)J * 3 + 2) * n + e.z];
-      const double xr = px.x * py.x - px.y * py.y, xi = px.x * py.y + px.y * py.x;
-      const double er = xr * pz.x - xi * pz.y, ei = xr * pz.y + xi * pz.x;
-      ar += Z[J] * er; ai += Z[J] * ei;
-    }
+    const size_t q = ((size_t)e.x * n + e.y) * nh + e.z;
+    const cplx<T> v = nt[q], A = SZ[q];
     const double2 f = gf[g];                        // (vfac, efac)
     const double w = (double)e.w;
-    const double qr = f.x * (double)v.x * invN + f.y * ar, qi = f.x * (double)v.y * invN + f.y * ai;
+    const double qr = f.x * (double)v.x * invN + f.y * (double)A.x;
+    const double qi = f.x * (double)v.y * invN + f.y * (double)A.y;
     qq[g] = mk<T>((T)(w * qr), (T)(-w * qi));       // w conj(Q)
   }
 }
