@@ -19,8 +19,9 @@ the paper names, that it follows):
                    XC; energy and potential.
 * ``minimize``     L-BFGS on sqrt(n) at fixed electron number.
 * ``sei``          electron-ion and ion-ion static structure factors on |q|
-                   shells, the direct-sum form for large cells, trajectory
-                   averages (Methods, static structure factors).
+                   shells, and the direct-sum form for large cells (Methods,
+                   static structure factors; a trajectory average is the mean
+                   of the per-snapshot values).
 * ``forces``       Hellmann-Feynman forces on the ions (Methods, molecular
                    dynamics).
 * ``pressure``     P = -dF/dOmega under a homogeneous dilation (Results,
