@@ -47,3 +47,29 @@ def sii_shells(pos: np.ndarray, L: float, n: int, n_shells: int = 200):
     s = np.array([p2[m2 == v].mean() for v in values]) / len(pos)
     return q, s
 
+
+def sei_shells_direct(rho: np.ndarray, pos: np.ndarray, L: float, n_electrons: float, n_shells: int = 200):
+    """sei_shells for large cells: the same definition, with S(G) summed
+    directly over the ions only for the wave vectors of the requested shells
+    (the full-grid structure factor of ~1000 ions on 256^3 is out of reach on
+    a CPU).  n_e(G) still comes from the full transform of rho."""
+    n = rho.shape[0]
+    Omega = L ** 3
+    ne = Omega * fft3(rho)
+    m2 = m2_grid(n)
+    values = np.unique(m2[m2 > 0])[:n_shells]
+    q = 2.0 * math.pi / L * np.sqrt(values.astype(float))
+    m = np.rint(np.fft.fftfreq(n) * n).astype(np.int64)
+    s = np.empty(len(values))
+    pos = np.asarray(pos, dtype=float)
+    # the grid vectors of all requested shells in one scan, grouped by m^2
+    flat = m2.ravel()
+    sel = np.nonzero((flat > 0) & (flat <= values[-1]))[0]
+    sel = sel[np.argsort(flat[sel], kind="stable")]
+    bounds = np.searchsorted(flat[sel], np.concatenate([values, [values[-1] + 1]]))
+    for i in range(len(values)):
+        ix, iy, iz = np.unravel_index(sel[bounds[i]:bounds[i + 1]], m2.shape)
+        G = 2.0 * math.pi / L * np.stack([m[ix], m[iy], m[iz]], axis=1).astype(float)
+        S = np.exp(-1j * (G @ pos.T)).sum(axis=1)
+        s[i] = float(np.mean((ne[ix, iy, iz] * np.conj(S)).real))
+    return q, s / math.sqrt(n_electrons * len(pos))
