@@ -214,17 +214,22 @@ def run_ours(args, rank, world, local):
     plan.profile_enable(False)
     host_pos = cell.pos.copy()
     host_rho = torch.empty(cell.n ** 3, dtype=torch.float32, pin_memory=True)
+    # Each step is timed on the host clock from the positions' copy-in to the
+    # density on the host; the L2 flush between steps stays outside, as for value.
     barrier()
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for _ in range(args.steps):
         flush_l2(flush)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         plan.structure_factor(host_pos)
         out = plan.minimize(rho, start_uniform=True, tol_F_per_ion=TOL_F, tol_residual=TOL_R)
         host_rho.copy_(rho, non_blocking=True)
         torch.cuda.synchronize(dev)
+        e2e_s += time.perf_counter() - t0
         if not out["converged"]:
             raise RuntimeError("e2e snapshot did not converge")
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(e2e_s)
     res["e2e"] = dict(seconds=e2e_s, h2d=host_pos.nbytes, d2h=host_rho.numel() * 4 + 11 * 8)
     plan_bytes = plan.lib.ofdft_plan_bytes
     plan.close()
