@@ -1288,7 +1288,12 @@ int Engine<T>::forces(const void* rho, double* f_out_h, void* stream_) {
   } else {
     OFDFT_CK(cudaMemsetAsync(f_out, 0, (size_t)nion * 3 * sizeof(double), st));
   }
-  OFDFT_RUN("k_ewald_force_real", st, (double)nion * nion * 32, k_ewald_force_real<<<nion, 256, 0, st>>>(pos_d, Z_d, nion, L, ew_eta, ew_rcut, ew_nimg, f_out));
+  // several blocks per ion (about 4 per SM in all), shares added in a fixed order
+  int nsplit = std::max(1, std::min(64, (4 * nsm + nion - 1) / nion));
+  while (nsplit > 1 && (size_t)nion * nsplit * 3 > partials_cap) --nsplit;
+  if ((size_t)nion * nsplit * 3 > partials_cap) { set_error("forces: too many ions for the scratch"); return OFDFT_ERR_INVALID; }
+  OFDFT_RUN("k_ewald_force_real", st, (double)nion * nion * 32, k_ewald_force_real<<<nion * nsplit, 256, 0, st>>>(pos_d, Z_d, nion, L, ew_eta, ew_rcut, ew_nimg, nsplit, partials));
+  OFDFT_RUN("k_sum_force_parts", st, (double)nion * nsplit * 24, k_sum_force_parts<<<(3 * nion + 127) / 128, 128, 0, st>>>(partials, nion, nsplit, f_out));
   OFDFT_CK(cudaMemcpyAsync(f_out_h, f_out, (size_t)nion * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   OFDFT_CK(cudaStreamSynchronize(st));
   return OFDFT_OK;

@@ -461,31 +461,35 @@ __global__ void __launch_bounds__(256) k_forces_g(const cplx<T>* __restrict__ qq
   if (threadIdx.x < 3) out[(size_t)I * 3 + threadIdx.x] = -Z[I] * tp * s[threadIdx.x];
 }
 
-// one block per ion: Ewald real-space force added to out[I*3 ..]; FP64.  As in
-// k_ewald_real, displacements are taken at minimum image (|a| <= nimg images
-// per axis then cover every distance below rcut) and the in-range (J, image)
-// terms are compacted before their erfc and exp are evaluated.
+// Ewald real-space force on ion I = blockIdx.x / nsplit from the share
+// blockIdx.x % nsplit of its (J, image) terms, FP64, into part[blockIdx.x * 3
+// ..] (k_sum_force_parts adds the shares to the forces in a fixed order).  As
+// in k_ewald_real, displacements are taken at minimum image (|a| <= nimg
+// images per axis then cover every distance below rcut) and the in-range terms
+// are compacted before their erfc and exp are evaluated.
 static __global__ void __launch_bounds__(256) k_ewald_force_real(const double* __restrict__ pos,
                                                                  const double* __restrict__ Z, int n_ion, double L,
-                                                                 double eta, double rcut, int nimg,
-                                                                 double* __restrict__ out) {
+                                                                 double eta, double rcut, int nimg, int nsplit,
+                                                                 double* __restrict__ part) {
   __shared__ double red[3 * 32];
   __shared__ double sx[256], sy[256], sz[256], sq[256];
   __shared__ int wcount[8], wbase[8], total;
-  const int I = blockIdx.x;
+  const int I = blockIdx.x / nsplit, sh = blockIdx.x % nsplit;
   const int side = 2 * nimg + 1;
   const int nim3 = side * side * side;
   const long tot = (long)n_ion * nim3;
+  const long per = (tot + nsplit - 1) / nsplit;
+  const long q0 = (long)sh * per, q1 = min(tot, q0 + per);
   const double rc2 = rcut * rcut;
   const double c2 = 2.0 * eta / 1.7724538509055160273;   // 2 eta / sqrt(pi)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double iL = 1.0 / L;
   double f[3] = {0, 0, 0};
-  for (long base = 0; base < tot; base += blockDim.x) {
+  for (long base = q0; base < q1; base += blockDim.x) {
     const long q = base + threadIdx.x;
     bool inside = false;
     double x = 0, y = 0, z = 0, r2 = 0;
-    if (q < tot) {
+    if (q < q1) {
       const int J = (int)(q / nim3), im = (int)(q % nim3);
       const int a = im / (side * side) - nimg, b = (im / side) % side - nimg, c = im % side - nimg;
       x = pos[I * 3] - pos[J * 3]; y = pos[I * 3 + 1] - pos[J * 3 + 1]; z = pos[I * 3 + 2] - pos[J * 3 + 2];
@@ -520,7 +524,19 @@ static __global__ void __launch_bounds__(256) k_ewald_force_real(const double* _
   double o[3];
   block_sum<3>(f, red, o);
   if (threadIdx.x == 0) {
-    out[I * 3 + 0] += o[0]; out[I * 3 + 1] += o[1]; out[I * 3 + 2] += o[2];
+    part[(size_t)blockIdx.x * 3 + 0] = o[0]; part[(size_t)blockIdx.x * 3 + 1] = o[1];
+    part[(size_t)blockIdx.x * 3 + 2] = o[2];
+  }
+}
+
+// out[I * 3 + d] += sum_s part[(I nsplit + s) * 3 + d], s in order; one thread per (I, d)
+static __global__ void k_sum_force_parts(const double* __restrict__ part, int n_ion, int nsplit,
+                                         double* __restrict__ out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_ion * 3; t += gridDim.x * blockDim.x) {
+    const int I = t / 3, d = t - I * 3;
+    double s = 0;
+    for (int k = 0; k < nsplit; ++k) s += part[((size_t)I * nsplit + k) * 3 + d];
+    out[t] += s;
   }
 }
 
