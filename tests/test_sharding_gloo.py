@@ -50,7 +50,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_time_and_count():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a threaded process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0][0] == out[1][0] == 2.0            # the slowest rank's time
