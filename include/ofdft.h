@@ -342,8 +342,9 @@ int ofdft_set_tiles(ofdft_plan* plan, const int* tile);
  *
  * The first call on a device looks up the array's device address on that
  * device (make that first call before capturing the stream into a graph).
- * All calls share the one array: calls whose GPU work overlaps race on it and
- * give wrong results, so serialise them.
+ * All calls on a device share its one array, so they run one at a time: a
+ * process-wide lock per device is held from the first copy into the array to
+ * the final synchronisation (calls from other host threads wait for it).
  */
 int ofdft_sei_shells_static(const double* rho, const double* pos, int n_ion, double L, int n,
                             double n_electrons, int n_shells, double* q_out, double* s_out,

@@ -56,8 +56,11 @@ static __device__ __align__(256) unsigned char g_sei_scratch[kScratchBytes];
 // once per device with that device current.
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+// One call at a time per device: the calls share the device's scratch array,
+// and each holds its device's lock until its stream has drained.
+std::mutex g_call_mu[kMaxDevices];
 
-int scratch_for_current_device(unsigned char** out) {
+int scratch_for_current_device(unsigned char** out, int* dev_out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { set_error(std::string("cudaGetDevice failed: ") + cudaGetErrorString(e)); return OFDFT_ERR_CUDA; }
@@ -73,6 +76,7 @@ int scratch_for_current_device(unsigned char** out) {
     g_scratch_addr[dev] = p;
   }
   *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *dev_out = dev;
   return OFDFT_OK;
 }
 
@@ -217,8 +221,10 @@ extern "C" int ofdft_sei_shells_static(const double* rho, const double* pos, int
     H.tw_h[t] = make_double2((double)cosl(a), (double)sinl(a));
   }
   unsigned char* base = nullptr;
-  int rc = scratch_for_current_device(&base);
+  int dev_idx = 0;
+  int rc = scratch_for_current_device(&base, &dev_idx);
   if (rc) return rc;
+  std::lock_guard<std::mutex> call_lock(g_call_mu[dev_idx]);   // released after the final synchronise
   double2* spec = reinterpret_cast<double2*>(base);
   double2* tw_n = reinterpret_cast<double2*>(base + kOffTwN);
   double2* tw_h = reinterpret_cast<double2*>(base + kOffTwH);

@@ -70,3 +70,37 @@ def test_static_sei_rejects_requests_beyond_its_fixed_size():
     assert "64" in _lib.last_error()
     small = torch.ones(32 ** 3, dtype=torch.float64, device="cuda")
     assert lib.ofdft_sei_shells_static(p(small), p(pos), 5, cell.L, 32, 5.0, 300, p(out), p(out), st) == _lib.OFDFT_ERR_INVALID
+
+
+def test_static_sei_concurrent_calls_give_the_sequential_results():
+    """Two host threads, each on its own stream, call the entry point on
+    different grids at the same time; the per-device lock keeps them off each
+    other's scratch, so every result equals the one-at-a-time result."""
+    import threading
+    lib = _lib.load()
+    cells = [random_cell(SEED_BASE + 44, 12, 1.0, 2.0, 1.0, 48), random_cell(SEED_BASE + 45, 9, 1.0, 1.6, 0.8, 32)]
+    rhos = [torch.tensor(_density(c, 20 + i), dtype=torch.float64, device="cuda") for i, c in enumerate(cells)]
+    poss = [torch.tensor(c.pos, dtype=torch.float64, device="cuda") for c in cells]
+    ref = [_static_call(lib, r, p, c, 100) for c, r, p in zip(cells, rhos, poss)]
+    out = [[], []]
+    errors = []
+
+    def worker(k):
+        try:
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                for _ in range(6):
+                    out[k].append(_static_call(lib, rhos[k], poss[k], cells[k], 100))
+        except Exception as e:          # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in (0, 1)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for k in (0, 1):
+        assert len(out[k]) == 6
+        for q, s in out[k]:
+            assert np.array_equal(q, ref[k][0]) and np.array_equal(s, ref[k][1])
