@@ -27,6 +27,36 @@ def test_fft_convention_matches_naive_dft():
     assert np.allclose(ifft3(F), f, atol=1e-13)
 
 
+@pytest.mark.parametrize("n", [4, 5, 6, 7, 8, 9])
+def test_fft_every_entry_against_brute_force_dft(n):
+    # every G of an n^3 grid (odd and even n): the O(N^2) sum written out
+    # over all r at once, with the 1/N of the forward convention
+    rng = np.random.default_rng(100 + n)
+    f = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    r = np.array(list(itertools.product(range(n), repeat=3)), dtype=float)       # [N, 3]
+    m = np.array(list(itertools.product(range(n), repeat=3)), dtype=float)       # [N, 3]
+    phase = np.exp(-2j * math.pi * (m @ r.T) / n)                                 # [N_G, N_r]
+    ref = (phase @ f.reshape(-1)).reshape(n, n, n) / n ** 3
+    F = fft3(f)
+    assert np.max(np.abs(F - ref)) < 1e-14 * max(1.0, np.max(np.abs(ref))) * n ** 2
+    # Parseval with this normalisation: sum_r |f|^2 = N sum_G |f~|^2
+    assert abs(np.sum(np.abs(f) ** 2) - n ** 3 * np.sum(np.abs(F) ** 2)) < 1e-11 * np.sum(np.abs(f) ** 2)
+    # the inverse returns the real field: round trip of the real part
+    assert np.max(np.abs(ifft3(fft3(f.real)) - f.real)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [5, 8, 9])
+def test_fft_single_plane_wave_is_a_delta(n):
+    # f(r) = exp(i G0.r) with G0 = (2 pi / L) m0 has f~ = 1 at m0 and 0 elsewhere
+    m0 = (1, n - 2, 3 % n)
+    x = np.arange(n)
+    f = np.exp(2j * math.pi * (m0[0] * x[:, None, None] + m0[1] * x[None, :, None] + m0[2] * x[None, None, :]) / n)
+    F = fft3(f)
+    expect = np.zeros((n, n, n), dtype=complex)
+    expect[m0] = 1.0
+    assert np.max(np.abs(F - expect)) < 1e-14
+
+
 def test_uniform_density_closed_form():
     c = fcc_cell()
     F = Functional(c)

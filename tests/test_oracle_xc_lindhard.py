@@ -104,3 +104,25 @@ def test_kernel_wang_teter_limit():
         got = kernel_value(q, nbar, T, mu0, dmu)
         assert abs(got - ref) < 1e-4 * abs(ref), (q, got, ref)
     assert kernel_value(0.0, nbar, T, mu0, dmu) == 0.0
+
+
+def test_kernel_large_q_limit_at_low_temperature():
+    # For large eta = q/(2 kF), F_L = 1/(3 eta^2) + 1/(15 eta^4) + O(eta^-6), so
+    # 1/F_L - 3 eta^2 - 1 -> -8/5: the kernel tends to -(8/5)(pi^2/kF) over
+    # the prefactor 2 a^2 nbar^(2a-2), approached as 1/eta^2.
+    nbar = 0.02
+    kf = (3 * math.pi ** 2 * nbar) ** (1 / 3)
+    T = 2e-4 * 0.5 * kf * kf
+    _, mu0, dmu = mean_density_params(nbar, T)
+    pref = 2 * ALPHA ** 2 * nbar ** (2 * ALPHA - 2)
+    limit = -1.6 * math.pi ** 2 / kf / pref
+    errs = []
+    for eta in (4.0, 8.0):
+        q = 2 * kf * eta
+        FL = 0.5 + (1 - eta * eta) / (4 * eta) * math.log((eta + 1) / (eta - 1))
+        exact = math.pi ** 2 / kf * (1 / FL - 3 * eta * eta - 1) / pref
+        got = kernel_value(q, nbar, T, mu0, dmu)
+        assert abs(got - exact) < 1e-6 * abs(exact), (eta, got, exact)
+        errs.append(abs(got / limit - 1))
+    # doubling eta divides the distance to the limit by about 4
+    assert errs[1] < 2e-3 and 0.2 < errs[1] / errs[0] < 0.3
