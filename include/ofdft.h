@@ -97,7 +97,8 @@ typedef struct {
 /* Minimiser options (L-BFGS on sqrt(n), strong-Wolfe line search). */
 typedef struct {
     double tol_F_per_ion; /* |dF|/N_ion below this for 3 consecutive iterations ...   */
-    double tol_residual;  /* ... and residual below this, Ha                           */
+    double tol_residual;  /* ... and residual below this, Ha (both >= 0; 0 is never
+                             met, so the minimiser runs to max_iter)                   */
     int m;                /* L-BFGS memory (1..8)                                      */
     int max_iter;         /* iteration cap                                             */
     double c1, c2;        /* Wolfe constants (sufficient decrease, curvature)          */

@@ -102,11 +102,24 @@ static int validate(const ofdft_cell* c, const ofdft_opts* o) {
   if (c->n_ion < 1 || !c->Z) { set_error("need n_ion >= 1 and Z"); return OFDFT_ERR_INVALID; }
   for (int i = 0; i < c->n_ion; ++i)
     if (!(c->Z[i] > 0) || !std::isfinite(c->Z[i])) { set_error("every Z must be positive"); return OFDFT_ERR_INVALID; }
-  if (!(c->rc > 0)) { set_error("rc must be positive"); return OFDFT_ERR_INVALID; }
+  if (!(c->rc > 0) || !std::isfinite(c->rc)) { set_error("rc must be positive and finite"); return OFDFT_ERR_INVALID; }
   if (!(c->T > 0) || !std::isfinite(c->T)) { set_error("T must be positive"); return OFDFT_ERR_INVALID; }
   if (o->precision != OFDFT_FP64 && o->precision != OFDFT_FP32) { set_error("bad precision"); return OFDFT_ERR_INVALID; }
   if (o->terms < 0 || o->terms > OFDFT_TERMS_ALL) { set_error("bad terms mask"); return OFDFT_ERR_INVALID; }
   if (!(o->alpha > 0 && o->alpha < 1)) { set_error("alpha must be in (0, 1)"); return OFDFT_ERR_INVALID; }
+  return OFDFT_OK;
+}
+
+// Minimiser options, checked alike by the single, batched and MD entry points.
+static int validate_min_opts(const ofdft_min_opts& o, const char* who) {
+  if (o.m < 1 || o.m > 8 || o.max_iter < 1 || !(o.c1 > 0) || !(o.c2 > o.c1) || !(o.c2 < 1)) {
+    set_error(std::string(who) + ": bad minimiser options (m in 1..8, max_iter >= 1, 0 < c1 < c2 < 1)");
+    return OFDFT_ERR_INVALID;
+  }
+  if (!(o.tol_F_per_ion >= 0) || !(o.tol_residual >= 0)) {
+    set_error(std::string(who) + ": bad minimiser options (tolerances must be >= 0, not NaN)");
+    return OFDFT_ERR_INVALID;
+  }
   return OFDFT_OK;
 }
 
@@ -191,14 +204,11 @@ int ofdft_energy_potential_async(ofdft_plan* plan, const void* rho, void* v_out,
 
 int ofdft_minimize(ofdft_plan* plan, void* rho_io, int start_uniform, const ofdft_min_opts* o, ofdft_result* r,
                    void* stream) {
-  if (!plan || !rho_io) { set_error("plan and rho_io must not be NULL"); return OFDFT_ERR_INVALID; }
   ofdft_min_opts d;
   ofdft_default_min_opts(&d);
   const ofdft_min_opts& oo = o ? *o : d;
-  if (oo.m < 1 || oo.m > 8 || oo.max_iter < 1 || !(oo.c1 > 0) || !(oo.c2 > oo.c1) || !(oo.c2 < 1)) {
-    set_error("bad minimiser options (m in 1..8, max_iter >= 1, 0 < c1 < c2 < 1)");
-    return OFDFT_ERR_INVALID;
-  }
+  if (int rc = validate_min_opts(oo, "ofdft_minimize")) return rc;
+  if (!plan || !rho_io) { set_error("plan and rho_io must not be NULL"); return OFDFT_ERR_INVALID; }
   return plan->eng->minimize(rho_io, start_uniform, oo, r, stream);
 }
 
@@ -222,6 +232,7 @@ int ofdft_md_run(ofdft_plan* plan, void* rho_io, int start_uniform, double* pos_
                  ofdft_md_frame* frames, double* q_out, double* sei_sum, double* sii_sum, void* stream) {
   if (!plan || !rho_io || !pos_io || !vel_io || !mass || !o || !th_io) { set_error("NULL argument"); return OFDFT_ERR_INVALID; }
   if (n_steps < 0 || !(o->dt > 0)) { set_error("ofdft_md_run: n_steps >= 0 and dt > 0 required"); return OFDFT_ERR_INVALID; }
+  if (int rc = validate_min_opts(o->min, "ofdft_md_run")) return rc;
   if (o->n_shells > 0 && (!q_out || !sei_sum || !sii_sum)) { set_error("ofdft_md_run: shell outputs required"); return OFDFT_ERR_INVALID; }
   if (!std::isfinite(o->dt) || !std::isfinite(o->T_ion) || (o->T_ion > 0 && !(o->tau > 0 && std::isfinite(o->tau)))) {
     set_error("ofdft_md_run: dt, T_ion must be finite; a thermostat (T_ion > 0) needs a finite tau > 0");
@@ -268,6 +279,7 @@ int ofdft_minimize_batch(ofdft_plan* const* plans, void* const* rhos, int count,
   ofdft_min_opts d;
   ofdft_default_min_opts(&d);
   const ofdft_min_opts oo = o ? *o : d;
+  if (int rc = validate_min_opts(oo, "ofdft_minimize_batch")) return rc;
   // largest grids first
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;

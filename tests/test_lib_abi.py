@@ -60,7 +60,8 @@ def test_plan_bytes_and_validation(lib):
     cell, keep = _cell(C)
     b = lib.ofdft_plan_bytes(ctypes.byref(cell), ctypes.byref(o))
     assert b > 20 * 32 ** 3 * 4
-    for bad in (dict(n=33), dict(n=14), dict(L=-1.0), dict(T=0.0), dict(Z=(3.0, -1.0)), dict(n=1024)):
+    for bad in (dict(n=33), dict(n=14), dict(L=-1.0), dict(T=0.0), dict(Z=(3.0, -1.0)), dict(n=1024),
+                dict(rc=float("inf")), dict(rc=float("nan")), dict(T=float("nan")), dict(L=float("inf"))):
         kw = dict(n=32, Z=(3.0, 3.0), L=7.6, T=0.2)
         kw.update(bad)
         c2, keep2 = _cell(C, **kw)
@@ -94,3 +95,24 @@ def test_fft_factorisations_cover_workload_grids():
         if _is_smooth(n):
             cell, keep = _cell(C, n=n)
             assert lib.ofdft_plan_bytes(ctypes.byref(cell), ctypes.byref(o)) > 0, n
+
+
+def test_minimiser_options_checked_alike_by_every_entry_point(lib):
+    # the options are checked before anything touches a plan or the GPU
+    from paper_2601_23002_gb300 import _lib as C
+    good = C.MinOpts(1e-6, 1e-4, 8, 100, 1e-4, 0.9)
+    bads = [C.MinOpts(1e-6, 1e-4, 0, 100, 1e-4, 0.9), C.MinOpts(1e-6, 1e-4, 9, 100, 1e-4, 0.9),
+            C.MinOpts(1e-6, 1e-4, 8, 0, 1e-4, 0.9), C.MinOpts(1e-6, 1e-4, 8, 100, 0.5, 0.4),
+            C.MinOpts(1e-6, 1e-4, 8, 100, 1e-4, 1.0), C.MinOpts(float("nan"), 1e-4, 8, 100, 1e-4, 0.9),
+            C.MinOpts(1e-6, -1.0, 8, 100, 1e-4, 0.9)]
+    for o in bads:
+        assert lib.ofdft_minimize(None, None, 1, ctypes.byref(o), None, None) == C.OFDFT_ERR_INVALID
+        assert "minimiser options" in C.last_error()
+        assert lib.ofdft_minimize_batch(None, None, 0, 1, ctypes.byref(o), None, 1) == C.OFDFT_ERR_INVALID
+    # valid options: the NULL plan is what fails; an empty batch has nothing to do
+    assert lib.ofdft_minimize(None, None, 1, ctypes.byref(good), None, None) == C.OFDFT_ERR_INVALID
+    assert "NULL" in C.last_error()
+    assert lib.ofdft_minimize_batch(None, None, 0, 1, ctypes.byref(good), None, 1) == C.OFDFT_OK
+    # zero tolerances are allowed (never met: the minimiser runs to max_iter)
+    zero = C.MinOpts(0.0, 0.0, 8, 100, 1e-4, 0.9)
+    assert lib.ofdft_minimize_batch(None, None, 0, 1, ctypes.byref(zero), None, 1) == C.OFDFT_OK
