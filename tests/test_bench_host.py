@@ -1,0 +1,62 @@
+"""Host logic of the benchmark's JSON line, on CPU: the roofline object of
+the dominant kernel and the DRAM-traffic lookup keyed by the kernel sources'
+hash."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_roofline_takes_the_kernel_with_the_largest_device_time(monkeypatch):
+    monkeypatch.setattr(bench, "load_peaks", lambda: (6000.0, "measured"))
+    monkeypatch.setattr(bench, "load_traffic", lambda name: 1.5e6 if name == "k_b" else None)
+    # {name: (launches, total ms, algorithmic bytes)}
+    prof = {"k_a": (10, 1.0, 10 * 2e6), "k_b": (4, 2.0, 4 * 6e6), "k_c": (1, 0.5, 1e6)}
+    r = bench.roofline(prof)
+    assert r["kernel"] == "k_b" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    # 6 MB per launch in 0.5 ms = 12 GB/s
+    assert r["achieved"] == pytest.approx(12.0)
+    assert r["peak"] == 6000.0 and r["frac"] == pytest.approx(12.0 / 6000.0, abs=1e-4)
+    assert r["traffic"] == 1.5e6 and r["launches"] == 4 and r["avg_us"] == pytest.approx(500.0)
+    assert r["share"] == pytest.approx(2.0 / 3.5, abs=1e-4)
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in r
+
+
+def test_traffic_only_for_the_kernel_sources_it_was_measured_on(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({
+        "k_zinv_epi": {"dram_bytes_per_launch_full_size": 2.5e7, "source_hash": "abc"},
+        "k_zfwd": {"dram_bytes_per_launch_full_size": 1.3e7, "source_hash": "old"}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    assert bench.load_traffic("k_zinv_epi") == 2.5e7
+    assert bench.load_traffic("k_zfwd") is None          # measured on other sources
+    assert bench.load_traffic("k_plane") is None         # never measured
+
+
+def test_peaks_come_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6783.5}))
+    assert bench.load_peaks() == (6783.5, "measured")
+
+
+def test_source_hash_ignores_the_host_only_abi_file(tmp_path, monkeypatch):
+    # the hash covers the files that define kernels and launch shapes; an edit
+    # of the C-ABI's host checks (api.cu) leaves it, an edit of a kernel does not
+    import shutil
+    src = os.path.join(bench.ROOT, "paper_2601_23002_gb300", "csrc")
+    dst = tmp_path / "paper_2601_23002_gb300" / "csrc"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("__pycache__"))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    assert len(h0) == 16
+    with open(dst / "api.cu", "a") as f:
+        f.write("\n// host-side edit\n")
+    assert bench.kernel_source_hash() == h0
+    with open(dst / "passes.cuh", "a") as f:
+        f.write("\n// kernel-side edit\n")
+    assert bench.kernel_source_hash() != h0
