@@ -81,9 +81,15 @@ class Server:
             finally:
                 plan.close()
 
-    def _worker(self) -> None:
+    def _slot_stream(self):
         torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(device=self.device)
+        return torch.cuda.Stream(device=self.device)
+
+    def _free_bytes(self) -> int:
+        return torch.cuda.mem_get_info(self.device)[0]
+
+    def _worker(self) -> None:
+        stream = self._slot_stream()
         while True:
             with self._lock:
                 while not self._stop and not self._ready():
@@ -97,6 +103,8 @@ class Server:
                 self._serve_one(req, stream)
             except OfdftError as e:
                 req.error = str(e)
+            except Exception as e:       # e.g. an allocation failure: the request fails, the slot lives on
+                req.error = f"{type(e).__name__}: {e}"
             req.finished = time.perf_counter() - self._t0
             with self._lock:
                 self._committed -= req.nbytes
@@ -142,8 +150,7 @@ class Server:
         for r in reqs:
             r.nbytes = self._plan_bytes(r.cell)
         reqs.sort(key=lambda r: r.arrival)
-        free, _ = torch.cuda.mem_get_info(self.device)
-        self._budget = free - self.reserve
+        self._budget = self._free_bytes() - self.reserve
         if any(r.nbytes > self._budget for r in reqs):
             raise ValueError("a request does not fit in device memory even alone")
         self._pending = reqs
