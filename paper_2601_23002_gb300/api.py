@@ -66,6 +66,12 @@ class Plan:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def _field(self, t: torch.Tensor, name: str):
         n = self.n
         if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == n ** 3):
@@ -259,5 +265,9 @@ def plan_for_cell(cell, precision="fp64", terms=C.TERMS_ALL, alpha=0.5, stream=N
     L, n, Z, pos, rc, T)."""
     p = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=precision, terms=terms, alpha=alpha,
              stream=stream)
-    p.structure_factor(cell.pos)
+    try:
+        p.structure_factor(cell.pos)
+    except BaseException:
+        p.close()          # free the device memory now, not at garbage collection
+        raise
     return p
