@@ -115,14 +115,21 @@ class ClockSampler:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
         except Exception:
             rows = []
+        rows = [r for r in rows if len(r) >= 9]      # a partial last line when the sampler stopped
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        smax = max(float(r[2]) for r in rows)
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:                        # "[N/A]" and the like
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        smx = [v for v in (num(r[2]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
-                "samples": len(rows)}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smx) if smx else None,
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ------------------------------------------------------------------ our arm

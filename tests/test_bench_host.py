@@ -60,3 +60,23 @@ def test_source_hash_ignores_the_host_only_abi_file(tmp_path, monkeypatch):
     with open(dst / "passes.cuh", "a") as f:
         f.write("\n// kernel-side edit\n")
     assert bench.kernel_source_hash() != h0
+
+
+def test_clock_summary_reads_median_max_and_active_reasons(tmp_path):
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clocks.csv")
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1965, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, [N/A], [N/A], [N/A], 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2040, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2040, 20"]                       # cut off when the sampler stopped
+    (tmp_path / "clocks.csv").write_text("\n".join(rows) + "\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2040.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+
+
+def test_clock_summary_without_samples(tmp_path):
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "missing.csv")
+    assert c.summary()["reasons"] == ["unsampled"]
