@@ -315,7 +315,13 @@ int ofdft_minimize_batch(ofdft_plan* const* plans, void* const* rhos, int count,
  * for each candidate schedule on this plan and keeps the fastest; the choice
  * is cached per (grid size, precision) for the process, so later plans of the
  * same size reuse it without timing.  Requires ofdft_structure_factor first.
- * us_per_eval (may be NULL) receives the measured evaluation time.
+ * tile (may be NULL) receives the chosen schedule; us_per_eval (may be NULL)
+ * the measured evaluation time, or -1 when a cached schedule was reused.
+ * ofdft_set_tiles installs a schedule directly: tile[0] in 8..64, tile[1] and
+ * tile[2] powers of two in 8..64, and the blocks' shared memory within the
+ * 227 KB a block may use; otherwise it returns OFDFT_ERR_INVALID and keeps the
+ * old schedule.  The schedule changes launch shapes only, never results
+ * beyond rounding order.  (Launch shape; no counterpart in the paper.)
  */
 int ofdft_autotune(ofdft_plan* plan, void* stream, int* tile, double* us_per_eval);
 int ofdft_set_tiles(ofdft_plan* plan, const int* tile);
