@@ -46,6 +46,7 @@ class Plan:
         self._p = ctypes.c_void_p()
         _check(self.lib.ofdft_plan_create(ctypes.byref(self.cell), ctypes.byref(self.opts),
                                           _stream_ptr(stream), ctypes.byref(self._p)))
+        self.device = torch.cuda.current_device()     # the plan's memory lives here
 
     @staticmethod
     def plan_bytes(L, n, Z, T, rc=1.0, precision="fp64", terms=C.TERMS_ALL, alpha=0.5) -> int:
@@ -72,28 +73,39 @@ class Plan:
     def __exit__(self, *exc):
         self.close()
 
+    def _on_device(self, t: torch.Tensor) -> bool:
+        return t.is_cuda and t.device.index == self.device
+
     def _field(self, t: torch.Tensor, name: str):
+        # the kernels read and write exactly n^3 elements of the plan's type on
+        # the plan's device: anything else is refused here, before any launch
         n = self.n
-        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.numel() == n ** 3):
-            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor with {n}^3 elements")
+        if not (self._on_device(t) and t.dtype == self.dtype and t.is_contiguous() and t.numel() == n ** 3):
+            raise ValueError(f"{name} must be a contiguous {self.dtype} tensor with {n}^3 elements "
+                             f"on cuda:{self.device}")
         return ctypes.c_void_p(t.data_ptr())
 
     def structure_factor(self, pos, S_out: torch.Tensor | None = None):
+        ni = self._Z.size
         if isinstance(pos, torch.Tensor) and pos.is_cuda:
+            if not (self._on_device(pos) and pos.numel() == 3 * ni):
+                raise ValueError(f"pos must hold {ni} x 3 positions on cuda:{self.device}")
             p = pos.contiguous().to(torch.float64)
             self._pos_keep = p
             ptr, dev = ctypes.c_void_p(p.data_ptr()), 1
         else:
             a = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
+            if a.size != 3 * ni:
+                raise ValueError(f"pos must hold {ni} x 3 positions, got {a.size} values")
             self._pos_keep = a
             ptr, dev = ctypes.c_void_p(a.ctypes.data), 0
         sptr = None
         if S_out is not None:
             nh = self.n // 2 + 1
             want = torch.complex64 if self.dtype == torch.float32 else torch.complex128
-            if not (S_out.is_cuda and S_out.dtype == want and S_out.is_contiguous()
+            if not (self._on_device(S_out) and S_out.dtype == want and S_out.is_contiguous()
                     and S_out.numel() == self.n * self.n * nh):
-                raise ValueError("S_out must be a contiguous CUDA complex tensor [n, n, n/2+1]")
+                raise ValueError("S_out must be a contiguous complex tensor [n, n, n/2+1] on the plan's device")
             sptr = ctypes.c_void_p(S_out.data_ptr())
         _check(self.lib.ofdft_structure_factor(self._p, ptr, dev, sptr, _stream_ptr(self.stream)))
 
@@ -113,7 +125,7 @@ class Plan:
         written to, without synchronising the stream."""
         if e_out is None:
             e_out = torch.empty(11, dtype=torch.float64, device=rho.device)
-        if not (e_out.is_cuda and e_out.dtype == torch.float64 and e_out.is_contiguous() and e_out.numel() >= 11):
+        if not (self._on_device(e_out) and e_out.dtype == torch.float64 and e_out.is_contiguous() and e_out.numel() >= 11):
             raise ValueError("e_out must be a contiguous CUDA float64 tensor with 11 elements")
         vp = self._field(v_out, "v_out") if v_out is not None else None
         _check(self.lib.ofdft_energy_potential_async(self._p, self._field(rho, "rho"), vp,
