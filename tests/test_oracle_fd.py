@@ -125,3 +125,17 @@ def test_thermodynamic_consistency():
     fm, _, _ = fd.tf_free_energy_density(n - h, T)
     _, v, _ = fd.tf_free_energy_density(n, T)
     assert np.allclose((fp - fm) / (2 * h), v, rtol=1e-7)
+
+
+def test_golden_file_is_what_its_generator_writes():
+    # the stored values come from tests/golden/make_fd_values.py (mpmath only)
+    pytest.importorskip("mpmath")
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_fd_values", os.path.join(HERE, "golden", "make_fd_values.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    stored = golden()
+    fresh = mod.values()
+    assert len(stored) == len(fresh)
+    for (nu, eta, val), (nu2, eta2, v2) in zip(stored, fresh):
+        assert (nu, eta) == (nu2, eta2) and val == float(v2)
