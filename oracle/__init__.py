@@ -11,6 +11,9 @@ the paper names, that it follows):
 
 * ``fermi_dirac``  Fermi-Dirac integrals, their inverse, the finite-T
                    Thomas-Fermi free energy (F_s^TF of Eq. 1).
+* ``fdint.c``,     the quadrature behind ``fermi_dirac`` in plain C
+  ``_native``      (panels of 20-point Gauss-Legendre in t with x = t^2),
+                   compiled with the host gcc into oracle/_build/.
 * ``xc``           Perdew-Zunger LDA exchange-correlation (Methods).
 * ``lindhard``     finite-T Lindhard response and the F_0^NL kernel (Eq. 2).
 * ``cell``         grid, G vectors, structure factor, local pseudopotential,
