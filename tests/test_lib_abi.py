@@ -116,3 +116,47 @@ def test_minimiser_options_checked_alike_by_every_entry_point(lib):
     # zero tolerances are allowed (never met: the minimiser runs to max_iter)
     zero = C.MinOpts(0.0, 0.0, 8, 100, 1e-4, 0.9)
     assert lib.ofdft_minimize_batch(None, None, 0, 1, ctypes.byref(zero), None, 1) == C.OFDFT_OK
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ofdft.h"
+
+int main(void) {
+    ofdft_opts o;
+    ofdft_default_opts(&o);
+    ofdft_min_opts m;
+    ofdft_default_min_opts(&m);
+    const double Z[2] = {3.0, 3.0};
+    ofdft_cell c = {.L = 7.6, .n = 32, .n_ion = 2, .Z = Z, .rc = 1.0, .T = 0.2};
+    size_t b = ofdft_plan_bytes(&c, &o);
+    c.n = 33;
+    size_t bad = ofdft_plan_bytes(&c, &o);
+    int rc = ofdft_minimize(NULL, NULL, 1, &m, NULL, NULL);
+    printf("%s|%zu|%zu|%d|%d|%s\n", ofdft_version(), b, bad, rc, m.m, ofdft_last_error());
+    return (b > 0 && bad == 0 && rc == OFDFT_ERR_INVALID) ? 0 : 1;
+}
+"""
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    # the boundary is a C ABI: a C99 program includes the header, links the
+    # shared library and calls its host-side entry points (no GPU needed)
+    import shutil
+    import subprocess
+    from paper_2601_23002_gb300 import _lib
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    _lib.load()                                        # builds the library if needed
+    so = _lib.LIB
+    src = tmp_path / "consumer.c"
+    src.write_text(C_CONSUMER)
+    exe = tmp_path / "consumer"
+    cc = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                         so, "-Wl,-rpath," + os.path.dirname(so), "-o", str(exe)], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, (run.stdout, run.stderr)
+    version, b, bad, rc, m, err = run.stdout.strip().split("|")
+    assert int(b) > 0 and int(bad) == 0 and int(m) == 8 and "NULL" in err
