@@ -71,6 +71,6 @@ def test_md_inputs():
         v = md_velocities(SEED_BASE + 7, mass, c.T)
         assert np.allclose((mass[:, None] * v).sum(0), 0.0, atol=1e-12)
         assert np.array_equal(v, md_velocities(SEED_BASE + 7, mass, c.T))
-        # the dense MD cells keep a hard core of 0.6 r_s (0.6 bohr at r_s = 1)
+        # the MD cells keep a hard core of 0.6 r_s, scaled with the density
         assert _min_image_distance(c.pos, c.L) >= 0.6 * c.meta["rs"] and c.n % 2 == 0 and _is_smooth(c.n)
         assert c.n >= c.L / (0.10 / 0.529177210903) - 1e-9        # 0.10 Angstrom or finer
