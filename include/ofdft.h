@@ -347,11 +347,13 @@ int ofdft_set_tiles(ofdft_plan* plan, const int* tile);
  *   s_out [n_shells], the k-th distinct nonzero |m|^2 shell in ascending order.
  * The call synchronises `stream` before returning.
  *
- * The first call on a device looks up the array's device address on that
- * device (make that first call before capturing the stream into a graph).
+ * Every call looks up the array's device address in the context current on
+ * the calling thread (a symbol lookup, which allocates nothing), so a caller
+ * that switches contexts or resets the device still gets its own copy.
  * All calls on a device share its one array, so they run one at a time: a
  * process-wide lock per device is held from the first copy into the array to
- * the final synchronisation (calls from other host threads wait for it).
+ * the final synchronisation, also when the call fails after queuing work
+ * (calls from other host threads wait for it).
  */
 int ofdft_sei_shells_static(const double* rho, const double* pos, int n_ion, double L, int n,
                             double n_electrons, int n_shells, double* q_out, double* s_out,

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "../../include/ofdft.h"
 #include "engine.h"
@@ -51,11 +52,13 @@ constexpr size_t kScratchBytes = ((kOffM2 + kStaticMaxShells * sizeof(int)) + 25
 
 static __device__ __align__(256) unsigned char g_sei_scratch[kScratchBytes];
 
-// Device address of g_sei_scratch for each device.  In host code the symbol
-// names a host-side stand-in, not device memory, so the address is looked up
-// once per device with that device current.
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+// Device address of g_sei_scratch in the context current on the calling
+// thread.  In host code the symbol names a host-side stand-in, not device
+// memory, so the address is looked up with cudaGetSymbolAddress.  The lookup
+// allocates nothing and is made on every call: a module's __device__ array
+// has one address per context, and a cached address would go stale when the
+// caller switches contexts on the same device (driver-API code with contexts
+// of its own) or resets the device.
 // One call at a time per device: the calls share the device's scratch array,
 // and each holds its device's lock until its stream has drained.
 std::mutex g_call_mu[kMaxDevices];
@@ -65,20 +68,27 @@ int scratch_for_current_device(unsigned char** out, int* dev_out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { set_error(std::string("cudaGetDevice failed: ") + cudaGetErrorString(e)); return OFDFT_ERR_CUDA; }
   if (dev < 0 || dev >= kMaxDevices) { set_error("device index out of range"); return OFDFT_ERR_INVALID; }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_sei_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error(std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      return OFDFT_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_sei_scratch);
+  if (e != cudaSuccess || !p) {
+    set_error(std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+    return OFDFT_ERR_CUDA;
   }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(p);
   *dev_out = dev;
   return OFDFT_OK;
 }
+
+// Waits for `st` when it goes out of scope while armed: an error return after
+// work has been queued on the scratch array must not release the device's
+// lock before that work has finished.
+struct DrainOnExit {
+  cudaStream_t st;
+  bool armed = false;
+  ~DrainOnExit() {
+    if (armed) { cudaStreamSynchronize(st); cudaGetLastError(); }
+  }
+};
 
 // Host-side staging for the tables that are copied into the scratch array
 // (fixed size, per thread, so the call allocates no host memory either).
@@ -225,6 +235,7 @@ extern "C" int ofdft_sei_shells_static(const double* rho, const double* pos, int
   int rc = scratch_for_current_device(&base, &dev_idx);
   if (rc) return rc;
   std::lock_guard<std::mutex> call_lock(g_call_mu[dev_idx]);   // released after the final synchronise
+  DrainOnExit drain{st};                 // declared after the lock: drains before it is released
   double2* spec = reinterpret_cast<double2*>(base);
   double2* tw_n = reinterpret_cast<double2*>(base + kOffTwN);
   double2* tw_h = reinterpret_cast<double2*>(base + kOffTwH);
@@ -241,6 +252,7 @@ extern "C" int ofdft_sei_shells_static(const double* rho, const double* pos, int
       return OFDFT_ERR_CUDA;                                                                 \
     }                                                                                        \
   } while (0)
+  drain.armed = true;                    // from the first copy into the array on
   NA_CK(cudaMemcpyAsync(tw_n, H.tw_n, n * sizeof(double2), cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(tw_h, H.tw_h, h * sizeof(double2), cudaMemcpyHostToDevice, st));
   NA_CK(cudaMemcpyAsync(idx, H.idx, (size_t)nent * sizeof(long long), cudaMemcpyHostToDevice, st));
@@ -286,6 +298,7 @@ extern "C" int ofdft_sei_shells_static(const double* rho, const double* pos, int
   NA_CK(cudaGetLastError());
   // the host tables above are reused by the next call on this thread
   NA_CK(cudaStreamSynchronize(st));
+  drain.armed = false;
 #undef NA_CK
   return OFDFT_OK;
 }

@@ -104,3 +104,27 @@ def test_static_sei_concurrent_calls_give_the_sequential_results():
         assert len(out[k]) == 6
         for q, s in out[k]:
             assert np.array_equal(q, ref[k][0]) and np.array_equal(s, ref[k][1])
+
+
+def test_static_sei_at_its_largest_grid_and_shell_count():
+    """n = 64 with 256 shells, the sizes the fixed array was laid out for: the
+    shells' half-spectrum entries (counted here on the host) stay within the
+    array's 16384 slots, and the result equals the plan entry point's."""
+    h = 32
+    m2s = sorted({mx * mx + my * my + mz * mz for mx in range(-h, h) for my in range(-h, h)
+                  for mz in range(h + 1)} - {0})[:256]
+    want = set(m2s)
+    entries = sum(1 for mx in range(-h, h) for my in range(-h, h) for mz in range(h + 1)
+                  if mx * mx + my * my + mz * mz in want)
+    assert entries <= 16384
+    lib = _lib.load()
+    cell = random_cell(SEED_BASE + 46, 20, 1.0, 2.2, 0.7, 64)
+    rho = torch.tensor(_density(cell, 30), dtype=torch.float64, device="cuda")
+    pos = torch.tensor(cell.pos, dtype=torch.float64, device="cuda")
+    plan = og.plan_for_cell(cell)
+    q_ref, s_ref = plan.sei_shells(rho, 256)
+    plan.close()
+    for _ in range(2):
+        q, s = _static_call(lib, rho, pos, cell, 256)
+        assert np.allclose(q, q_ref, rtol=1e-14, atol=0)
+        assert np.max(np.abs(s - s_ref)) < 1e-10
