@@ -13,10 +13,14 @@ Convergence: |dF| / N_ion below tol_F for 3 consecutive iterations and the
 Euler-Lagrange residual R = (int n (v - mu)^2 / N_e)^(1/2) below tol_R.
 
 Optional preconditioning (precond_c = c): the two-loop recursion starts from
-H0 = gamma P instead of gamma I, with P f = IFFT[c / (c + G^2/2) f~], the
-inverse of the vW kinetic operator shifted by c; the first direction is -P g.
-Any symmetric positive-definite H0 leaves the minimum unchanged; the tests
-check that both forms reach the same one.
+H0 = gamma P instead of gamma I, with P f = IFFT[c / h(G) f~],
+h(G) = c + G^2/2 (the vW kinetic operator shifted by c); the first direction
+is -P g.  Two optional terms model more of the psi-Hessian at the mean
+density: precond_k = f_K adds f_K 4 a^2 nbar^(2a-1) K(G) (the nonlocal
+kernel's curvature), precond_h = f_H adds f_H 8 pi nbar / G^2 (a density wave
+2 sqrt(nbar) dpsi against the Hartree energy) for G != 0; h is kept above
+c / 1000.  Any symmetric positive-definite H0 leaves the minimum unchanged;
+the tests check that the forms reach the same one.
 """
 from __future__ import annotations
 
@@ -109,7 +113,7 @@ def line_search(phi, phi0, dphi0, t0, c1=1e-4, c2=0.9, max_evals=30):
 
 
 def lbfgs(functional, psi0=None, m=8, c1=1e-4, c2=0.9, tol_F=1e-6, tol_R=1e-4,
-          max_iter=1000, verbose=False, precond_c=None) -> MinResult:
+          max_iter=1000, verbose=False, precond_c=None, precond_k=0.0, precond_h=0.0) -> MinResult:
     """L-BFGS on psi (see module docstring).  functional.evaluate_psi(psi)
     returns (energies, gradient, rho)."""
     F = functional
@@ -118,7 +122,13 @@ def lbfgs(functional, psi0=None, m=8, c1=1e-4, c2=0.9, tol_F=1e-6, tol_R=1e-4,
         P = lambda v: v
     else:
         from .functional import fft3, ifft3
-        pg = precond_c / (precond_c + 0.5 * F.G2)
+        h = precond_c + 0.5 * F.G2
+        if precond_k:
+            h = h + precond_k * 4.0 * F.alpha ** 2 * F.nbar ** (2.0 * F.alpha - 1.0) * F.K
+        if precond_h:
+            with np.errstate(divide="ignore"):
+                h = h + np.where(F.G2 > 0, precond_h * 8.0 * math.pi * F.nbar / np.where(F.G2 > 0, F.G2, 1.0), 0.0)
+        pg = precond_c / np.maximum(h, 1e-3 * precond_c)
         P = lambda v: ifft3(fft3(v) * pg)
     n_ion = float(len(F.cell.Z))
     dot = lambda a, b: dV * float(np.sum(a * b))

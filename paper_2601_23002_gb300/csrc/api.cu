@@ -90,12 +90,12 @@ static bool smooth235(int k) {
 static int validate(const ofdft_cell* c, const ofdft_opts* o) {
   if (!c || !o) { set_error("cell and opts must not be NULL"); return OFDFT_ERR_INVALID; }
   if (!(c->L > 0) || !std::isfinite(c->L)) { set_error("L must be positive"); return OFDFT_ERR_INVALID; }
-  if (c->n < 8 || c->n > 512 || c->n % 2 || !smooth235(c->n)) {
-    set_error("n must be even, 2,3,5-smooth and in [8, 512]");
+  if (c->n < 8 || c->n > 512 || !smooth235(c->n)) {
+    set_error("n must be 2,3,5-smooth and in [8, 512]");
     return OFDFT_ERR_INVALID;
   }
   int rad[8], np;
-  if (!factor_radices(c->n, rad, &np) || !factor_radices(c->n / 2, rad, &np)) {
+  if (!factor_radices(c->n, rad, &np) || (c->n % 2 == 0 && !factor_radices(c->n / 2, rad, &np))) {
     set_error("n has no supported radix factorisation");
     return OFDFT_ERR_INVALID;
   }

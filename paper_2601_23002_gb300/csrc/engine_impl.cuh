@@ -78,6 +78,9 @@ class Engine : public IEngine {
   CellSpec cs;
   int n = 0, nh = 0, h = 0;
   size_t N = 0, NH = 0;
+  // length of the minimiser's vectors: N rounded up to whole 16-byte groups
+  // of the streaming passes (odd n); the padding is zero and stays zero
+  size_t Nv = 0;
   double L = 0, Omega = 0, dV = 0, Ne = 0, nbar = 0, Te = 0;
   int m_max = 8;
   FftPlan1 pn{}, ph{};
@@ -240,28 +243,36 @@ class Engine : public IEngine {
   // rho or psi and d rows
   size_t zinv_bytes(int r) const {
     const int nact = spectra().nact;
-    const int P = (n / 2 + 1) | 1;
-    return (size_t)nact * r * (n / 2 + 1) * sizeof(C) + 2 * (size_t)r * P * sizeof(C) + 2 * (size_t)r * n * sizeof(T);
+    return (size_t)nact * r * (n / 2 + 1) * sizeof(C) + 2 * zbuf_elems(n, r, zpitch()) * sizeof(C) +
+           2 * (size_t)r * n * sizeof(T);
   }
+  // row pitch of the z passes' FFT buffers: odd and >= the transform length
+  // (n / 2 + 1 half-length rows for even n; length-n rows of two packed real
+  // rows for odd n)
+  int zpitch() const { return (n & 1) ? n : ((n / 2 + 1) | 1); }
 
   void geometry() {
     n = cs.n; h = n / 2; nh = h + 1;
     N = (size_t)n * n * n;
     NH = (size_t)n * n * nh;
+    Nv = (N + 3) & ~(size_t)3;
     L = cs.L; Omega = L * L * L; dV = Omega / (double)N;
     Ne = 0; for (double z : cs.Z) Ne += z;
     nbar = Ne / Omega; Te = cs.T;
     zR = std::max(1, std::min(16, 1024 / h));     // 16 rows per block: best in a sweep at 128^3
-    zP = nh | 1;                                  // odd row pitch >= h + 1
+    zP = zpitch();
     yJ = sizeof(T) == 4 ? 16 : 8;
     xJ = yJ;
     // overrides (autotuner, set_tiles, OFDFT_ZR/YJ/XJ) only within the shapes
     // the reduction scratch was sized for: at least 8 rows / 8 columns
     if (tune.zR >= 8 && tune.zR <= 64) zR = tune.zR;
+    // odd n: the z passes pair rows, and an even row count keeps every
+    // block's rows on an 8-byte boundary
+    if (n & 1) zR = std::max(2, zR & ~1);
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
     if (tune.yJ >= 8 && tune.yJ <= 64 && pow2(tune.yJ)) yJ = tune.yJ;
     if (tune.xJ >= 8 && tune.xJ <= 64 && pow2(tune.xJ)) xJ = tune.xJ;
-    smem_zf = align16((size_t)2 * zR * n * sizeof(T)) + 2 * (size_t)zR * zP * sizeof(C);
+    smem_zf = align16((size_t)2 * zR * n * sizeof(T)) + 2 * zbuf_elems(n, zR, zP) * sizeof(C);
     // (the G-space and epilogue passes reuse their tiles as reduction scratch)
     smem_zi = std::max(zinv_bytes(zR), tree_scratch_bytes<T>(12, kThreads));   // finalize: 12 columns
     smem_y = 2 * (size_t)n * yJ * sizeof(C);
@@ -278,12 +289,13 @@ class Engine : public IEngine {
     // cluster launch waits for pairs of free SMs (64 cells of 48^3-96^3:
     // 712 -> 669 snapshots/s with clusters)
     smem_pl2 = ((size_t)(n / 2) * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int);
-    prec2 = plane_allowed && prec2_allowed && n >= 112 && smem_pl2 <= (size_t)225 * 1024;
+    // (even n only: the pair splits the plane's rows in two equal halves)
+    prec2 = plane_allowed && prec2_allowed && n >= 112 && n % 2 == 0 && smem_pl2 <= (size_t)225 * 1024;
     // streaming vector kernels: a multiple of the SM count (4 resident blocks
     // per SM); the async-copy ring kernels hold 160 KB of shared memory, one
     // block per SM
     grid_vec = (int)std::min<size_t>((size_t)4 * nsm, (N + kThreads - 1) / kThreads);
-    grid_stream = (int)std::min<size_t>((size_t)nsm, (N / StreamCfg<T>::K + kStreamThreads - 1) / kStreamThreads);
+    grid_stream = (int)std::min<size_t>((size_t)nsm, (Nv / StreamCfg<T>::K + kStreamThreads - 1) / kStreamThreads);
   }
 
   size_t plan_bytes_estimate() {
@@ -291,7 +303,7 @@ class Engine : public IEngine {
     size_t b = 0;
     b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
     if (planes) b += NH * sizeof(C);                         // vloc in plane order
-    b += (6 + 3 * (size_t)m_max) * N * sizeof(T);            // psi d g gp, P g x2, history s y P y
+    b += (6 + 3 * (size_t)m_max) * Nv * sizeof(T);           // psi d g gp, P g x2, history s y P y
     b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
     b += (size_t)(n + h) * sizeof(C);
     return b;
@@ -307,12 +319,15 @@ class Engine : public IEngine {
     geometry();
     // (64-point halves at 128^3: radices 8, 8 rather than 16, 4 -- 128 butterflies per stage for a
     // 16-row block instead of 64 in the radix-16 stage; z passes measured 1-2% faster)
-    if (!factor_radices(n, pn.radix, &pn.npass) || !factor_radices_balanced(h, ph.radix, &ph.npass)) {
+    if (!factor_radices(n, pn.radix, &pn.npass) || (n % 2 == 0 && !factor_radices_balanced(h, ph.radix, &ph.npass))) {
       set_error("grid size not supported by the FFT radices");
       return OFDFT_ERR_INVALID;
     }
     pn.n = n; ph.n = h;
-    if (const char* zr = std::getenv("OFDFT_ZRADIX")) {
+    // odd n: the z passes transform pairs of real rows at full length
+    const int nzt = (n & 1) ? n : h;          // length of the z passes' transforms
+    if (n & 1) ph = pn;
+    if (const char* zr = (n & 1) ? nullptr : std::getenv("OFDFT_ZRADIX")) {
       // override of the z passes' half-length radices for tuning, e.g. "8,8"
       // (used only if they are supported and multiply to n/2)
       FftPlan1 q{};
@@ -333,19 +348,19 @@ class Engine : public IEngine {
     if (prec2) prec2_kern = plane_prec2_kernel<T>(radix_mask(pn));
     int rc;
     // twiddles
-    std::vector<C> twn(n), twh(h);
+    std::vector<C> twn(n), twh(nzt);
     for (int t = 0; t < n; ++t) {
       long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)n;
       twn[t] = mk<T>((T)cosl(a), (T)sinl(a));
     }
-    for (int t = 0; t < h; ++t) {
-      long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)h;
+    for (int t = 0; t < nzt; ++t) {
+      long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)nzt;
       twh[t] = mk<T>((T)cosl(a), (T)sinl(a));
     }
     if ((rc = alloc(&tw_n, n))) return rc;
-    if ((rc = alloc(&tw_h, h))) return rc;
+    if ((rc = alloc(&tw_h, nzt))) return rc;
     OFDFT_CK(cudaMemcpyAsync(tw_n, twn.data(), n * sizeof(C), cudaMemcpyHostToDevice, st));
-    OFDFT_CK(cudaMemcpyAsync(tw_h, twh.data(), h * sizeof(C), cudaMemcpyHostToDevice, st));
+    OFDFT_CK(cudaMemcpyAsync(tw_h, twh.data(), nzt * sizeof(C), cudaMemcpyHostToDevice, st));
     // buffers
     for (int f = 0; f < 3; ++f)
       if ((rc = alloc(&spec[f], NH))) return rc;
@@ -372,16 +387,25 @@ class Engine : public IEngine {
       OFDFT_CK(cudaMemcpyAsync(rev_d, rev.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
       if (planes && (rc = alloc(&vloc_pl, NH))) return rc;
     }
-    if ((rc = alloc(&psi, N))) return rc;
-    if ((rc = alloc(&d, N))) return rc;
-    if ((rc = alloc(&g, N))) return rc;
-    if ((rc = alloc(&gp, N))) return rc;
-    if ((rc = alloc(&pgv[0], N))) return rc;
-    if ((rc = alloc(&pgv[1], N))) return rc;
-    for (int i = 0; i < m_max; ++i) {
-      if ((rc = alloc(&Sh[i], N))) return rc;
-      if ((rc = alloc(&Yh[i], N))) return rc;
-      if ((rc = alloc(&PYh[i], N))) return rc;
+    {
+      T** vecs[6] = {&psi, &d, &g, &gp, &pgv[0], &pgv[1]};
+      for (T** v : vecs)
+        if ((rc = alloc(v, Nv))) return rc;
+      for (int i = 0; i < m_max; ++i) {
+        if ((rc = alloc(&Sh[i], Nv))) return rc;
+        if ((rc = alloc(&Yh[i], Nv))) return rc;
+        if ((rc = alloc(&PYh[i], Nv))) return rc;
+      }
+      if (Nv > N) {
+        // zero padding: the grid kernels write [0, N) only, the streaming
+        // passes map zeros to zeros there, so the padding adds nothing to a dot
+        for (T** v : vecs) OFDFT_CK(cudaMemsetAsync(*v + N, 0, (Nv - N) * sizeof(T), st));
+        for (int i = 0; i < m_max; ++i) {
+          OFDFT_CK(cudaMemsetAsync(Sh[i] + N, 0, (Nv - N) * sizeof(T), st));
+          OFDFT_CK(cudaMemsetAsync(Yh[i] + N, 0, (Nv - N) * sizeof(T), st));
+          OFDFT_CK(cudaMemsetAsync(PYh[i] + N, 0, (Nv - N) * sizeof(T), st));
+        }
+      }
     }
     const int nm2 = 3 * h * h + 1;
     if ((rc = alloc(&Kd, nm2))) return rc;
@@ -406,32 +430,56 @@ class Engine : public IEngine {
     if ((rc = raise_smem_limits())) return rc;
     // mean-density ideal gas: eta0, mu0, dmu0/dn
     const double y = 9.8696044010893586188 * nbar / (1.4142135623730950488 * pow(Te, 1.5));
-    OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, 32, 0, st>>>(y, Te, res_d));
+    OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, kMeanThreads, 0, st>>>(y, Te, res_d));
     OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     OFDFT_CK(cudaStreamSynchronize(st));
     std::memcpy(mean_params, res_h, 4 * sizeof(double));
     if (use_na()) {
       KernArgs ka{L, nbar, Te, mean_params[1], mean_params[2], cs.alpha, nm2};
-      OFDFT_RUN("k_kernel_table", st, (double)nm2 * 8, k_kernel_table<<<(nm2 + 127) / 128, 128, 0, st>>>(ka, Kd));
+      OFDFT_RUN("k_kernel_table", st, (double)nm2 * 8, k_kernel_table<<<kernel_table_blocks(nm2), 32 * kKernWarps, 0, st>>>(ka, Kd));
     } else {
       OFDFT_CK(cudaMemsetAsync(Kd, 0, nm2 * sizeof(double), st));
     }
     OFDFT_RUN("k_convert_table", st, (double)nm2 * (8 + sizeof(T)), k_convert_table<T><<<(nm2 + 255) / 256, 256, 0, st>>>(Kd, Kt, nm2));
     {
-      // kinetic preconditioner of the minimiser: p(G) = c / (c + G^2/2).  The
-      // psi-Hessian of the Thomas-Fermi term at the mean density is about
-      // 2 mu + 4 n dmu/dn, ~4 E_F degenerate and ~4 T classical, so below
-      // G^2/2 ~ 4 (E_F + T) it, not the vW term, sets the curvature.
-      // c = 4 (E_F + T) was the best of a scan (0.5-12) over the 128^3 cell,
-      // 64 batched cells and 60 serving cells (11, 20.2 and 20.1 evaluations
-      // on average); OFDFT_PREC_C replaces the factor 4, for such studies.
+      // preconditioner of the minimiser: p(G) = c / h(G), h(G) a model of the
+      // psi-Hessian at the mean density per unit |dpsi~(G)|^2:
+      //   h(G) = c + G^2/2 + f_K 4 a^2 nbar^(2a-1) K(G) + f_H 8 pi nbar / G^2.
+      // c stands for the Thomas-Fermi term: its psi-Hessian at the mean
+      // density is about 2 mu + 4 n dmu/dn, ~4 E_F degenerate and ~4 T
+      // classical; c = 4 (E_F + T).  G^2/2 is the vW term.  The nonlocal
+      // term's own curvature is its kernel K(G) (a = 1/2), and a density wave
+      // dn = 2 sqrt(nbar) dpsi costs the Hartree energy (Omega/2) 4 pi
+      // |dn~|^2 / G^2, i.e. 8 pi nbar / G^2: in large cells this long-wavelength
+      // stiffness exceeds c at the smallest G (the 58.6-bohr 1024-ion cell:
+      // 22 c) and set the iteration count (131 evaluations without it).
+      // f_K = 1 and f_H = 1.5 (and the factor 4 of c) were the best of a scan
+      // over the 256^3 and 128^3 single cells, 16 batched and 17 served cells
+      // (68, 10, 254 and 230 evaluations); OFDFT_PREC_C, OFDFT_PREC_H and
+      // OFDFT_PREC_K replace the three factors, for such studies.
       const double kF = std::cbrt(3.0 * kPi * kPi * nbar);
       double cfac = 4.0;
       if (const char* ev = std::getenv("OFDFT_PREC_C")) cfac = std::atof(ev) > 0 ? std::atof(ev) : cfac;
       const double c = cfac * (0.5 * kF * kF + Te);
       const double tp2d = (2.0 * kPi / L) * (2.0 * kPi / L);
+      double hfac = (cs.terms & OFDFT_TERM_HARTREE) ? 1.5 : 0.0;
+      if (const char* ev = std::getenv("OFDFT_PREC_H")) hfac = std::atof(ev) >= 0 ? std::atof(ev) : hfac;
+      double kfac = use_na() ? 1.0 : 0.0;
+      if (const char* ev = std::getenv("OFDFT_PREC_K")) kfac = std::atof(ev);
+      std::vector<double> Kh;
+      if (kfac != 0.0 && use_na()) {
+        Kh.resize(nm2);
+        OFDFT_CK(cudaMemcpyAsync(Kh.data(), Kd, nm2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        OFDFT_CK(cudaStreamSynchronize(st));
+      }
+      const double kcurv = 4.0 * cs.alpha * cs.alpha * std::pow(nbar, 2.0 * cs.alpha - 1.0);
       std::vector<T> ph_(nm2);
-      for (int m2 = 0; m2 < nm2; ++m2) ph_[m2] = (T)(c / (c + 0.5 * tp2d * m2));
+      for (int m2 = 0; m2 < nm2; ++m2) {
+        const double hart = m2 > 0 ? hfac * 8.0 * kPi * nbar / (tp2d * m2) : 0.0;
+        const double kk = Kh.empty() ? 0.0 : kfac * kcurv * Kh[m2];
+        // (the kernel is negative at large G; h stays above c / 1000)
+        ph_[m2] = (T)(c / std::max(1e-3 * c, c + 0.5 * tp2d * m2 + hart + kk));
+      }
       if ((rc = alloc(&precT, nm2))) return rc;
       OFDFT_CK(cudaMemcpyAsync(precT, ph_.data(), nm2 * sizeof(T), cudaMemcpyHostToDevice, st));
       OFDFT_CK(cudaStreamSynchronize(st));
@@ -459,7 +507,7 @@ class Engine : public IEngine {
       n_vloc = 0;
       for (int kx = 0; kx < n; ++kx)
         for (int ky = 0; ky < n; ++ky) {
-          const int mx = kx <= h - 1 ? kx : kx - n, my = ky <= h - 1 ? ky : ky - n;
+          const int mx = kx <= (n - 1) / 2 ? kx : kx - n, my = ky <= (n - 1) / 2 ? ky : ky - n;
           for (int kz = 0; kz < nh; ++kz)
             if (tp2 * (double)(mx * mx + my * my + kz * kz) <= g2cut_loc) ++n_vloc;
         }
@@ -479,8 +527,7 @@ class Engine : public IEngine {
 
   bool tiles_fit(int r, int j) const {
     const size_t lim = 227 * 1024;
-    const int P = nh | 1;
-    const size_t zf = align16((size_t)2 * r * n * sizeof(T)) + 2 * (size_t)r * P * sizeof(C);
+    const size_t zf = align16((size_t)2 * r * n * sizeof(T)) + 2 * zbuf_elems(n, r, zpitch()) * sizeof(C);
     const size_t zi = zinv_bytes(r);
     const size_t yx = 3 * (size_t)n * j * sizeof(C);
     return r >= 8 && j >= 8 && (j & (j - 1)) == 0 && zf <= lim && zi <= lim && yx <= lim && j <= 64 && r <= 64;
@@ -614,15 +661,17 @@ class Engine : public IEngine {
     // without the full S(G), only rows with |mx|, |my| <= mlim can reach g2rows:
     // zero everything, then compute that square of rows
     int mlim = (int)std::floor(std::sqrt(g2rows) / (2.0 * kPi / L));
-    if (full || mlim > n / 2 - 1) mlim = -1;
+    if (full || mlim > (n - 1) / 2) mlim = -1;
     const int nrows = mlim < 0 ? n * n : (2 * mlim + 1) * (2 * mlim + 1);
     if (mlim >= 0) {
       OFDFT_CK(cudaMemsetAsync(Sg, 0, NH * sizeof(C), st));
       OFDFT_CK(cudaMemsetAsync(vloc, 0, NH * sizeof(C), st));
       OFDFT_CK(cudaMemsetAsync(SZg, 0, NH * sizeof(C), st));
     }
-    // ions per shared-memory chunk: staged kz phases within 40 KB
-    const int sch = std::max(1, std::min(64, (int)(40960 / ((size_t)nh * sizeof(C)))));
+    // ions per shared-memory chunk: staged kz phases within 36 KB, so that
+    // with the row phases (8 x 64 complex), the charges and the kernel's own
+    // static scratch the block stays inside the default 48 KB (FP64, n = 80)
+    const int sch = std::max(1, std::min(64, (int)(36864 / ((size_t)nh * sizeof(C)))));
     const size_t ssm = (size_t)sch * nh * sizeof(C) + (size_t)kStructRows * sch * sizeof(C) + (size_t)sch * sizeof(T);
     const int sgrid = (nrows + kStructRows - 1) / kStructRows;
     OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, SZg, partials));
@@ -795,7 +844,7 @@ class Engine : public IEngine {
       const int S = cn + nw <= 17 ? 3 : 2;   // k_gram is built for 2 or 3 ring stages
       const size_t sm = std::max(StreamCfg<T>::ring_bytes(S, cn + nw), tree_scratch_bytes<T>(cn * nw, kStreamThreads));
       prof.begin("k_gram", st, (double)(cn + nw) * N * sizeof(T));
-      auto launch = [&](auto kern) { kern<<<grid_stream, kStreamThreads, sm, st>>>(xl, cn, N, partials, counters + 1, o); };
+      auto launch = [&](auto kern) { kern<<<grid_stream, kStreamThreads, sm, st>>>(xl, cn, Nv, partials, counters + 1, o); };
       switch (nw * 8 + S) {
         case 1 * 8 + 3: launch(k_gram<T, 1, 3>); break;
         case 2 * 8 + 3: launch(k_gram<T, 2, 3>); break;
@@ -830,7 +879,7 @@ class Engine : public IEngine {
     xl.nv = nv + 2;
     OFDFT_RUN("k_lincomb", st, (double)(nv + 3) * N * sizeof(T),
               k_lincomb<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(kMaxLin - 1), nv + 2), st>>>(
-                  xl, nv, out, N, partials, counters + 2, res_d + 16, ts, dcoef));
+                  xl, nv, out, Nv, partials, counters + 2, res_d + 16, ts, dcoef));
     if (!dd) return OFDFT_OK;
     int rc;
     if ((rc = read_results(st))) return rc;
@@ -1103,7 +1152,7 @@ int Engine<T>::minimize(void* rho_io, int start_uniform, const ofdft_min_opts& o
     xa.nv = 4; xa.v[0] = psi; xa.v[1] = d; xa.v[2] = gp; xa.v[3] = g;
     OFDFT_RUN("k_accept", st, 8.0 * N * sizeof(T),
               k_accept<T><<<grid_stream, kStreamThreads, StreamCfg<T>::ring_bytes(stream_stages(4), 4), st>>>(
-                  xa, (T)acc.t, (T)(2.0 * lastScale), (T)(lastMu - mu_ref), psi, g, Sh[slot], Yh[slot], N,
+                  xa, (T)acc.t, (T)(2.0 * lastScale), (T)(lastMu - mu_ref), psi, g, Sh[slot], Yh[slot], Nv,
                   partials, counters + 3, res_d + 120));
     OFDFT_CK(cudaMemcpyAsync(res_h + 120, res_d + 120, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
     new_slot = slot;
@@ -1140,10 +1189,11 @@ int Engine<T>::build_shells(int n_shells, cudaStream_t st) {
   if (n_shells < 1 || n_shells > 4096) { set_error("n_shells must be in [1, 4096]"); return OFDFT_ERR_INVALID; }
   if (sh_ns == n_shells) return OFDFT_OK;
   // distinct nonzero m^2 present on the grid, ascending, and their entries
-  const int lim = n / 2;
+  // signed wave numbers on the grid: -(n/2) .. (n-1)/2 per axis; kz = 0 .. n/2
+  const int lim = n / 2, mhi = (n - 1) / 2;
   std::vector<char> present(3 * lim * lim + 1, 0);
-  for (int mx = -lim; mx < lim; ++mx)
-    for (int my = -lim; my < lim; ++my)
+  for (int mx = -lim; mx <= mhi; ++mx)
+    for (int my = -lim; my <= mhi; ++my)
       for (int mz = 0; mz <= lim; ++mz) {
         const int m2 = mx * mx + my * my + mz * mz;
         if (m2 > 0) present[m2] = 1;
@@ -1163,8 +1213,8 @@ int Engine<T>::build_shells(int n_shells, cudaStream_t st) {
   std::vector<std::vector<long long>> lists(ns);
   std::vector<std::vector<float>> wl(ns);
   const int r = (int)std::ceil(std::sqrt((double)m2max));
-  for (int mx = -std::min(r, lim); mx <= std::min(r, lim - 1); ++mx)
-    for (int my = -std::min(r, lim); my <= std::min(r, lim - 1); ++my)
+  for (int mx = -std::min(r, lim); mx <= std::min(r, mhi); ++mx)
+    for (int my = -std::min(r, lim); my <= std::min(r, mhi); ++my)
       for (int mz = 0; mz <= std::min(r, lim); ++mz) {
         const int m2 = mx * mx + my * my + mz * mz;
         if (m2 == 0 || m2 > m2max || shell_of[m2] < 0) continue;
@@ -1248,8 +1298,8 @@ int Engine<T>::forces(const void* rho, double* f_out_h, void* stream_) {
     std::vector<double2> gf;
     const int r = (int)std::ceil(std::sqrt(g2cut_loc) / tp);
     const bool loc = (cs.terms & OFDFT_TERM_LOC) != 0;
-    for (int mx = std::max(-h, -r); mx <= std::min(h - 1, r); ++mx)
-      for (int my = std::max(-h, -r); my <= std::min(h - 1, r); ++my)
+    for (int mx = std::max(-h, -r); mx <= std::min((n - 1) / 2, r); ++mx)
+      for (int my = std::max(-h, -r); my <= std::min((n - 1) / 2, r); ++my)
         for (int kz = 0; kz <= std::min(h, r); ++kz) {
           const int m2 = mx * mx + my * my + kz * kz;
           const double G2 = tp * tp * (double)m2;
@@ -1313,14 +1363,14 @@ int Engine<T>::build_pressure_table(cudaStream_t st) {
   for (int i = 0; i < 4; ++i) {
     const double nb = nbar / (lam[i] * lam[i] * lam[i]);
     const double y = 9.8696044010893586188 * nb / (1.4142135623730950488 * std::pow(Te, 1.5));
-    OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, 32, 0, st>>>(y, Te, mp + 4 * i));
+    OFDFT_RUN("k_mean_density", st, 32.0, k_mean_density<<<1, kMeanThreads, 0, st>>>(y, Te, mp + 4 * i));
   }
   std::vector<double> mph(16);
   OFDFT_CK(cudaMemcpyAsync(mph.data(), mp, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
   OFDFT_CK(cudaStreamSynchronize(st));
   for (int i = 0; i < 4; ++i) {
     KernArgs ka{L * lam[i], nbar / (lam[i] * lam[i] * lam[i]), Te, mph[4 * i + 1], mph[4 * i + 2], cs.alpha, nm2};
-    OFDFT_RUN("k_kernel_table", st, (double)nm2 * 8, k_kernel_table<<<(nm2 + 127) / 128, 128, 0, st>>>(ka, p_tab + (size_t)i * nm2));
+    OFDFT_RUN("k_kernel_table", st, (double)nm2 * 8, k_kernel_table<<<kernel_table_blocks(nm2), 32 * kKernWarps, 0, st>>>(ka, p_tab + (size_t)i * nm2));
   }
   std::vector<double> tabs((size_t)4 * nm2), K0(nm2), pnl(nm2);
   OFDFT_CK(cudaMemcpyAsync(tabs.data(), p_tab, tabs.size() * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -2,7 +2,9 @@
 //
 // One evaluation of F[n] and its potential is five launches over the grid:
 //   1. k_zfwd      prologue (n, n^a, psi from rho or from psi + t d) fused with
-//                  the real-to-complex FFT along z (half-length complex FFT).
+//                  the real-to-complex FFT along z (a half-length complex FFT
+//                  per row for even n, one length-n complex FFT per two rows
+//                  for odd n).
 //   2. k_ypass<-1> complex FFT along y.
 //   3. k_xgspace   FFT along x, every G-space term (Hartree + local
 //                  pseudopotential, nonlocal kernel K(|G|), vW |G|^2) with its
@@ -199,7 +201,15 @@ template <typename T> struct ProArgs {
   const double* dsc;
 };
 
-// smem: psit[R][n] (T) | dbuf[R][n] (T) | buf0[R][P] | buf1[R][P] (complex)
+// Rows of one z-pass FFT buffer: even n transforms each real row as a
+// half-length complex row (R rows of pitch P); odd n packs two real rows into
+// one complex row of length n (ceil(R/2) rows of pitch P = n).
+__host__ __device__ __forceinline__ size_t zbuf_elems(int n, int R, int P) {
+  return (n & 1) ? (size_t)((R + 1) >> 1) * P : (size_t)R * P;
+}
+
+// smem: psit[R][n] (T) | dbuf[R][n] (T) | buf0 | buf1 (complex, zbuf_elems each)
+// Odd n: ph is the full-length plan and tw_h the length-n twiddles.
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T> a, Spectra<T> sp, FftPlan1 ph,
                                               const cplx<T>* __restrict__ tw_h,
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
   T* psit = reinterpret_cast<T*>(smem_raw);
   T* dbuf = psit + (size_t)R * n;
   cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)2 * R * n * sizeof(T) + 15) & ~(size_t)15));
-  cplx<T>* buf1 = buf0 + (size_t)R * P;
+  cplx<T>* buf1 = buf0 + zbuf_elems(n, R, P);
   const size_t row0 = (size_t)blockIdx.x * R;
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
   const size_t off = row0 * n;
@@ -240,6 +250,46 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zfwd(ProArgs<T>
   const size_t nn = (size_t)n * n;
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
+    if (n & 1) {
+      // odd n: rows 2p and 2p + 1 as the real and imaginary parts of one
+      // length-n complex row z = x_a + i x_b; with Z = FFT(z),
+      //   X_a[k] = (Z[k] + Z*[n-k]) / 2,   X_b[k] = -i (Z[k] - Z*[n-k]) / 2
+      auto fv = [&](int i) -> T {       // field fid at buffer position i
+        const T x = psit[i];
+        if (fid == 2) return x - psi_shift;
+        const T nv = a.mode == 0 ? dbuf[i] : scale * x * x;
+        return fid == 0 ? nv : pow_t<T>(fmax(nv, nmin), alpha);
+      };
+      const int npair = (R + 1) >> 1;
+      const unsigned Mn = qmagic(n);
+      for (int q = threadIdx.x; q < npair * n; q += blockDim.x) {
+        const int pr = qdiv(q, n, Mn), j = q - pr * n;
+        const int rb = 2 * pr + 1;
+        buf0[pr * P + j] = mk<T>(fv(2 * pr * n + j), rb < R ? fv(rb * n + j) : (T)0);
+      }
+      __syncthreads();
+      cplx<T>* Z = fft_smem<T, -1>(buf0, buf1, ph, 1, P, npair, tw_h);
+      cplx<T>* out = sp.s[fid];
+      for (int q = threadIdx.x; q < R * nh; q += blockDim.x) {
+        int r, k;
+        if (sp.planes) { k = qdiv(q, R, MR); r = q - k * R; }
+        else { r = qdiv(q, nh, Mnh); k = q - r * nh; }
+        const cplx<T>* zr = Z + (r >> 1) * P;
+        const cplx<T> zk = zr[k];
+        const cplx<T> zc = cconj(zr[k == 0 ? 0 : n - k]);
+        cplx<T> o;
+        if ((r & 1) == 0) {
+          o = mk<T>((T)0.5 * (zk.x + zc.x), (T)0.5 * (zk.y + zc.y));
+        } else {
+          const cplx<T> dd = csub(zk, zc);
+          o = mk<T>((T)0.5 * dd.y, (T)-0.5 * dd.x);
+        }
+        const size_t at = sp.planes ? (size_t)k * nn + row0 + r : (row0 + r) * nh + k;
+        out[at] = o;
+      }
+      __syncthreads();
+      continue;
+    }
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
       const int r = qdiv(q, h, Mh), k = q - r * h;
       T x0 = psit[r * n + 2 * k], x1 = psit[r * n + 2 * k + 1];
@@ -388,8 +438,8 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
       if (in) {
         const int jl = (int)(j0 + j);
         const int ky = qdiv(jl, nh, Mnh), kz = jl - ky * nh;
-        const int mx = kx <= n / 2 - 1 ? kx : kx - n;
-        const int my = ky <= n / 2 - 1 ? ky : ky - n;
+        const int mx = kx <= (n - 1) / 2 ? kx : kx - n;
+        const int my = ky <= (n - 1) / 2 ? ky : ky - n;
         need = tp2 * (T)(mx * mx + my * my + kz * kz) <= g2cut;
       }
       cp_async_c(vbuf + q, g.vloc + (need ? (size_t)kx * plane + j0 + j : 0), need);
@@ -404,8 +454,8 @@ __global__ void __launch_bounds__(256) k_xgspace(Spectra<T> sp, GArgs<T> g, FftP
     if (j >= jn) { F[q] = mk<T>(0, 0); continue; }
     const int jl = (int)(j0 + j);                 // < n (n/2+1) <= 2^17
     const int ky = qdiv(jl, nh, Mnh), kz = jl - ky * nh;
-    const int mx = kx <= n / 2 - 1 ? kx : kx - n;
-    const int my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int mx = kx <= (n - 1) / 2 ? kx : kx - n;
+    const int my = ky <= (n - 1) / 2 ? ky : ky - n;
     const int m2 = mx * mx + my * my + kz * kz;
     const T G2 = tp2 * (T)m2;
     const T w = (kz == 0 || 2 * kz == n) ? (T)1 : (T)2;
@@ -556,8 +606,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
   const int h = n / 2, nh = h + 1;
   cplx<T>* stg = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* buf0 = stg + (size_t)sp.nact * R * nh;
-  cplx<T>* buf1 = buf0 + (size_t)R * P;
-  T* pin = reinterpret_cast<T*>(buf1 + (size_t)R * P);
+  cplx<T>* buf1 = buf0 + zbuf_elems(n, R, P);
+  T* pin = reinterpret_cast<T*>(buf1 + zbuf_elems(n, R, P));
   const size_t row0 = (size_t)blockIdx.x * R;
   const int Rfull = R;
   R = (int)min((size_t)R, (size_t)n * n - row0);     // rows in this block
@@ -581,16 +631,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
     }
   }
   {
-    // rows of rho (mode 0) or psi and d (mode 1) in 8-byte pieces (n is even,
-    // so every row starts on an 8-byte boundary)
+    // rows of rho (mode 0) or psi and d (mode 1) in 8-byte pieces: the block
+    // starts on an 8-byte boundary (n even, or an even number of rows per
+    // block); an odd element count leaves one element for a 4-byte copy
     constexpr int E = 8 / sizeof(T);
     const int pieces = tot / E;
     // (mode 3: the previous output pold, when P y = out - pold is wanted)
     const T* src0 = a.mode == 0 ? a.rho : (a.mode == 3 ? a.pold : a.psi);
-    const int npc = a.mode == 3 ? (a.pyout ? pieces : 0) : pieces;
+    const bool want = a.mode != 3 || a.pyout != nullptr;
+    const int npc = want ? pieces : 0;
     for (int q = threadIdx.x; q < npc; q += blockDim.x) {
       cp_async<8>(pin + q * E, src0 + off + q * E, true);
       if (a.mode == 1) cp_async<8>(pin + (size_t)Rfull * n + q * E, a.d + off + q * E, true);
+    }
+    if (want && pieces * E < tot && threadIdx.x == 0) {
+      const int q = tot - 1;                 // E = 2 and tot odd: the last float
+      cp_async<sizeof(T)>(pin + q, src0 + off + q, true);
+      if (a.mode == 1) cp_async<sizeof(T)>(pin + (size_t)Rfull * n + q, a.d + off + q, true);
     }
   }
   cp_async_commit();
@@ -602,6 +659,36 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
   for (int f = 0; f < sp.nact; ++f) {
     const int fid = sp.idx[f];
     cplx<T>* in = stg + (size_t)f * Rfull * nh;
+    if (n & 1) {
+      // odd n: rows 2p and 2p + 1 from one length-n inverse transform of
+      // Z[k] = A[k] + i B[k], A and B the rows' spectra extended by
+      // A[n-k] = A*[k] (the imaginary parts at k = 0 dropped, as a real
+      // inverse transform does); the result is a + i b
+      const int npair = (R + 1) >> 1;
+      const unsigned Mn = qmagic(n);
+      for (int q = threadIdx.x; q < npair * n; q += blockDim.x) {
+        const int pr = qdiv(q, n, Mn), k = q - pr * n;
+        const int rb = 2 * pr + 1;
+        const bool lo = k < nh;
+        const int kk = lo ? k : n - k;
+        cplx<T> A = in[2 * pr * nh + kk];
+        cplx<T> B = rb < R ? in[rb * nh + kk] : mk<T>((T)0, (T)0);
+        if (k == 0) { A.y = 0; B.y = 0; }
+        if (!lo) { A.y = -A.y; B.y = -B.y; }
+        buf0[pr * P + k] = mk<T>(A.x - B.y, A.y + B.x);
+      }
+      __syncthreads();                                 // staging slot f is now free
+      cplx<T>* z = fft_smem<T, +1>(buf0, buf1, ph, 1, P, npair, tw_h);
+      T* dst = reinterpret_cast<T*>(in);
+      for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        const int r = qdiv(q, n, Mn), j = q - r * n;
+        const cplx<T> v = z[(r >> 1) * P + j];
+        dst[q] = (r & 1) ? v.y : v.x;
+      }
+      realf[fid] = dst;
+      __syncthreads();
+      continue;
+    }
     // Z[k] = (X[k] + X*[h-k]) + i W^-k (X[k] - X*[h-k]),  k = 0..h-1
     for (int q = threadIdx.x; q < R * h; q += blockDim.x) {
       const int r = qdiv(q, h, Mh), k = q - r * h;

@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1) k_plane(Spectra<T> sp, GArgs
   for (int q = threadIdx.x; q < nn; q += blockDim.x) {
     const int px = qdiv(q, n, Mn), py = q - px * n;
     const int kx = rev[px], ky = rev[py];
-    const int mx = kx <= n / 2 - 1 ? kx : kx - n;
-    const int my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int mx = kx <= (n - 1) / 2 ? kx : kx - n;
+    const int my = ky <= (n - 1) / 2 ? ky : ky - n;
     const int m2 = mx * mx + my * my + kz * kz;
     const T G2 = tp2 * (T)m2;
     cplx<T>* cell = a + px * pitch + py;
@@ -349,8 +349,8 @@ k_plane_prec2(Spectra<T> sp, GArgs<T> g, FftPlan1 pn, const int* __restrict__ re
     const int r = qdiv(q, n, Mn), py = q - r * n;
     const int px = rank * half + r;
     const int kx = rev[px], ky = rev[py];
-    const int mx = kx <= n / 2 - 1 ? kx : kx - n;
-    const int my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int mx = kx <= (n - 1) / 2 ? kx : kx - n;
+    const int my = ky <= (n - 1) / 2 ? ky : ky - n;
     const int m2 = mx * mx + my * my + kz * kz;
     cplx<T>* cell = a + r * pitch + py;
     const cplx<T> v = *cell;

@@ -1,5 +1,5 @@
 // k_plane instantiated for the radix sets of the grid sizes the plane path
-// serves (even 2,3,5-smooth n up to 160; bit r set: radix r used by the
+// serves (2,3,5-smooth n up to 160, odd or even; bit r set: radix r used by the
 // fewest-pass factorisation of n), float plans.
 #include "plane.cuh"
 
@@ -34,6 +34,12 @@ PlaneKernel<float> plane_kernel<float>(unsigned mask) {
     case 0x10100u: return k_plane<float, 0x10100u>;
     case 0x10200u: return k_plane<float, 0x10200u>;
     case 0x10400u: return k_plane<float, 0x10400u>;
+    case 0x20u: return k_plane<float, 0x20u>;
+    case 0x28u: return k_plane<float, 0x28u>;
+    case 0x200u: return k_plane<float, 0x200u>;
+    case 0x208u: return k_plane<float, 0x208u>;
+    case 0x220u: return k_plane<float, 0x220u>;
+    case 0x228u: return k_plane<float, 0x228u>;
     default: return k_plane<float, kAllRadices>;
   }
 }

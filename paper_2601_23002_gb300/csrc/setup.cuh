@@ -15,7 +15,7 @@ static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n
   const int tot = n_ion * 3 * n;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += gridDim.x * blockDim.x) {
     const int k = q % n, d = (q / n) % 3, I = q / (3 * n);
-    const int m = k <= n / 2 - 1 ? k : k - n;
+    const int m = k <= (n - 1) / 2 ? k : k - n;
     double f = pos[I * 3 + d] / L;
     f -= floor(f);                       // wrap into [0, 1)
     // angle = -2 pi m f; reduce m f modulo 1 before the trig call
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __re
   auto row_of = [&](int rw, int& kx, int& ky, int& mx, int& my) {
     if (mlim < 0) {
       kx = rw / n; ky = rw % n;
-      mx = kx <= n / 2 - 1 ? kx : kx - n;
-      my = ky <= n / 2 - 1 ? ky : ky - n;
+      mx = kx <= (n - 1) / 2 ? kx : kx - n;
+      my = ky <= (n - 1) / 2 ? ky : ky - n;
     } else {
       mx = rw / side - mlim; my = rw % side - mlim;
       kx = mx < 0 ? mx + n : mx; ky = my < 0 ? my + n : my;
@@ -280,10 +280,17 @@ static __device__ double lind_panel_split(double a, double b, double q, double c
   return s * h;
 }
 
-static __global__ void k_kernel_table(KernArgs a, double* __restrict__ Kout) {
-  const int m2 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m2 >= a.nm2) return;
-  if (m2 == 0) { Kout[0] = 0.0; return; }
+// One warp per m^2 (kKernWarps warps per block): the lanes take the plain
+// panels and the graded levels in turn, and the lane sums are added by a
+// fixed shuffle tree, so the result does not depend on the launch.  (One
+// thread per m^2 left a small grid's table to a few hundred threads, each
+// integrating thousands of panels: 5.6 ms at 16^3.)
+constexpr int kKernWarps = 4;
+static __global__ void __launch_bounds__(32 * kKernWarps) k_kernel_table(KernArgs a, double* __restrict__ Kout) {
+  const int lane = threadIdx.x & 31;
+  const int m2 = blockIdx.x * kKernWarps + (threadIdx.x >> 5);
+  if (m2 >= a.nm2) return;                            // whole warps leave together
+  if (m2 == 0) { if (lane == 0) Kout[0] = 0.0; return; }
   const double q = 2.0 * kPi / a.L * sqrt((double)m2);
   const double T = a.T, mu0 = a.mu0;
   const double kmax = sqrt(2.0 * fmax(mu0 + 45.0 * T, 45.0 * T));
@@ -295,7 +302,7 @@ static __global__ void k_kernel_table(KernArgs a, double* __restrict__ Kout) {
   const double gc = c * occ_fd(c, mu0, T);
   // closed form of int ln|2k - q| dk: (1/2) [u ln|u| - u], u = 2k - q
   auto F = [](double u) { return u == 0 ? 0.0 : u * log(fabs(u)) - u; };
-  double integral = 0;   // int_0^kmax k f(k) [ln|(2k+q)/(2k-q)| - 4k/q] dk
+  double part = 0;   // this lane's share of int_0^kmax k f(k) [ln|(2k+q)/(2k-q)| - 4k/q] dk
   // graded region [ga, gb] around c (at least 2 panel widths on each side, so
   // that every plain panel stays >= 2h away from the singularity)
   const bool sing = c < kmax + 2.0 * h;
@@ -306,27 +313,31 @@ static __global__ void k_kernel_table(KernArgs a, double* __restrict__ Kout) {
     if (b0 <= a0) return;
     const int np = max(1, (int)ceil((b0 - a0) / h));
     const double hh = (b0 - a0) / np;
-    for (int p = 0; p < np; ++p) integral += lind_panel_plain(a0 + p * hh, a0 + (p + 1) * hh, q, mu0, T);
+    for (int p = lane; p < np; p += 32) part += lind_panel_plain(a0 + p * hh, a0 + (p + 1) * hh, q, mu0, T);
   };
   plain(0.0, ga);
   plain(gb, kmax);
   if (sing && gb > ga) {
-    // split at c (if inside), grade geometrically toward c from both ends
+    // split at c (if inside), grade geometrically toward c from both ends:
+    // level l covers [cl - w 2^-l, cl - w 2^-(l+1)] on the left (w = cl - ga)
+    // and [cl + w' 2^-(l+1), cl + w' 2^-l] on the right (w' = gb - cl), down
+    // to widths of 1e-15 (c + h), at most 48 levels a side
     const double cl = fmin(fmax(c, ga), gb);
-    double lo = ga, hi = cl, w = hi - lo;
-    for (int lev = 0; lev < 48 && w > 1e-15 * (c + h); ++lev) {
-      const double mid = hi - 0.5 * w;
-      integral += lind_panel_split(lo, mid, q, c, gc, mu0, T);
-      lo = mid; w = hi - lo;
+    const double wl = cl - ga, wr = gb - cl, wmin = 1e-15 * (c + h);
+    for (int lev = lane; lev < 96; lev += 32) {
+      const bool left = lev < 48;
+      const int l = left ? lev : lev - 48;
+      const double w = (left ? wl : wr) * ldexp(1.0, -l);
+      if (!(w > wmin)) continue;
+      if (left) part += lind_panel_split(cl - w, cl - 0.5 * w, q, c, gc, mu0, T);
+      else part += lind_panel_split(cl + 0.5 * w, cl + w, q, c, gc, mu0, T);
     }
-    lo = cl; hi = gb; w = hi - lo;
-    for (int lev = 0; lev < 48 && w > 1e-15 * (c + h); ++lev) {
-      const double mid = lo + 0.5 * w;
-      integral += lind_panel_split(mid, hi, q, c, gc, mu0, T);
-      hi = mid; w = hi - lo;
-    }
-    integral -= gc * 0.5 * (F(2.0 * gb - q) - F(2.0 * ga - q));
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane != 0) return;
+  double integral = part;
+  if (sing && gb > ga) integral -= gc * 0.5 * (F(2.0 * gb - q) - F(2.0 * ga - q));
   // chi0 = -(4 nbar / q^2)(1 + eps);  -1/chi0 - q^2/(4 nbar) = -(q^2/(4 nbar)) eps / (1 + eps)
   const double eps = integral * q / (4.0 * kPi * kPi * a.nbar);
   const double resp_excess = -q * q / (4.0 * a.nbar) * eps / (1.0 + eps);
@@ -334,16 +345,22 @@ static __global__ void k_kernel_table(KernArgs a, double* __restrict__ Kout) {
   Kout[m2] = (resp_excess - a.dmudn) / denom;
 }
 
-// I_{-1/2}(eta) = int_0^inf 2 / (1 + exp(t^2 - eta)) dt, one thread, FP64.
-static __global__ void k_mean_density(double y, double T, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Launch shape of k_kernel_table for nm2 entries.
+inline int kernel_table_blocks(int nm2) { return (nm2 + kKernWarps - 1) / kKernWarps; }
+
+// I_{-1/2}(eta) = int_0^inf 2 / (1 + exp(t^2 - eta)) dt at the mean density,
+// FP64: 400 panels of 10-point Gauss-Legendre, one panel per thread (one
+// block of kMeanThreads), summed by a fixed tree.
+constexpr int kMeanThreads = 512;
+static __global__ void __launch_bounds__(kMeanThreads) k_mean_density(double y, double T, double* out) {
+  __shared__ double red[kMeanThreads];
   double eta, p;
   fd_eta_p(y, eta, p);
   const double tmax = sqrt(fmax(eta, 0.0) + 60.0);
   const int npan = 400;
   const double h = tmax / npan;
   double s = 0;
-  for (int i = 0; i < npan; ++i) {
+  for (int i = threadIdx.x; i < npan; i += blockDim.x) {
     const double a = i * h, m = a + 0.5 * h;
     for (int j = 0; j < 10; ++j) {
       const double t = m + 0.5 * h * c_glx[j];
@@ -352,7 +369,14 @@ static __global__ void k_mean_density(double y, double T, double* out) {
       s += c_glw[j] * 2.0 * f;
     }
   }
-  const double im = s * 0.5 * h;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double im = red[0] * 0.5 * h;
   out[0] = eta;
   out[1] = T * eta;                                                      // mu0
   out[2] = 2.0 * kPi * kPi / (1.4142135623730950488 * sqrt(T) * im);     // dmu0/dn
@@ -451,9 +475,9 @@ __global__ void __launch_bounds__(256) k_forces_g(const cplx<T>* __restrict__ qq
     const cplx<T> eI = cmul(ab, c);
     const cplx<T> q = qq[g];
     const T im = q.x * eI.y + q.y * eI.x;          // Im[q e_I]
-    const int mx = e.x <= n / 2 - 1 ? e.x : e.x - n;
-    const int my = e.y <= n / 2 - 1 ? e.y : e.y - n;
-    const int mz = e.z <= n / 2 - 1 ? e.z : e.z - n;   // the phase tables' convention
+    const int mx = e.x <= (n - 1) / 2 ? e.x : e.x - n;
+    const int my = e.y <= (n - 1) / 2 ? e.y : e.y - n;
+    const int mz = e.z <= (n - 1) / 2 ? e.z : e.z - n;   // the phase tables' convention
     acc[0].add(im * (T)mx); acc[1].add(im * (T)my); acc[2].add(im * (T)mz);
   }
   double s[3];
@@ -590,7 +614,7 @@ __global__ void __launch_bounds__(256) k_pressure_g(const cplx<T>* __restrict__ 
     const int kz = (int)(q % nh);
     const size_t row = q / nh;
     const int kx = (int)(row / n), ky = (int)(row % n);
-    const int mx = kx <= n / 2 - 1 ? kx : kx - n, my = ky <= n / 2 - 1 ? ky : ky - n;
+    const int mx = kx <= (n - 1) / 2 ? kx : kx - n, my = ky <= (n - 1) / 2 ? ky : ky - n;
     const int m2 = mx * mx + my * my + kz * kz;
     const double w = (kz == 0 || 2 * kz == n) ? 1.0 : 2.0;
     if (vloc) {

@@ -59,6 +59,19 @@ def test_preconditioned_minimiser_reaches_the_same_minimum(small_min):
     assert r.iterations < r0.iterations
 
 
+def test_hartree_and_kernel_preconditioner_reaches_the_same_minimum(small_min):
+    # the preconditioner with the kernel's curvature and the Hartree term
+    # 8 pi nbar / G^2 is another symmetric positive-definite H0: same minimum
+    c, F0, r0 = small_min
+    F = Functional(c)
+    kF = (3 * math.pi ** 2 * c.n_electrons / c.volume) ** (1 / 3)
+    r = lbfgs(F, precond_c=4 * (0.5 * kF ** 2 + c.T), precond_k=1.0, precond_h=1.5, tol_F=1e-11,
+              tol_R=1e-8, max_iter=400)
+    assert r.converged
+    assert abs(r.energies["total"] - r0.energies["total"]) / c.n_ion < 1e-10
+    assert np.linalg.norm(r.rho - r0.rho) / np.linalg.norm(r0.rho) < 1e-6
+
+
 def test_sei_uniform_is_zero():
     c = random_cell(21, 8, 1.0, 1.5, 1.0, 16)
     q, s = sei_shells(np.full((16,) * 3, c.n_electrons / c.volume), c.pos, c.L, c.n_electrons, 40)
