@@ -86,12 +86,12 @@ def test_null_arguments_rejected(lib):
 
 
 def test_fft_factorisations_cover_workload_grids():
-    # every even 2,3,5-smooth grid 8..512 factors into the supported radices
+    # every 2,3,5-smooth grid 8..512, odd or even, factors into the supported radices
     from workloads.cells import _is_smooth
     from paper_2601_23002_gb300 import _lib as C
     lib = C.load()
     o = C.Opts(C.OFDFT_FP64, C.TERMS_ALL, 0.5)
-    for n in range(8, 513, 2):
+    for n in range(8, 513):
         if _is_smooth(n):
             cell, keep = _cell(C, n=n)
             assert lib.ofdft_plan_bytes(ctypes.byref(cell), ctypes.byref(o)) > 0, n

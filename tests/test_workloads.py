@@ -1,5 +1,5 @@
-"""The seeded synthetic inputs follow their stated recipe: grid sizes even
-and 2,3,5-smooth within their clamp, ions at least 0.8 bohr apart under the
+"""The seeded synthetic inputs follow their stated recipe: grid sizes the
+smallest 2,3,5-smooth n (odd or even) within their clamp, ions at least 0.8 bohr apart under the
 minimum image, cell sides from r_s, temperatures from theta, MD velocities
 without net momentum, and the same draws on every call."""
 import math
@@ -25,11 +25,14 @@ def _min_image_distance(pos, L):
 def test_grid_rule():
     for L in np.linspace(5.0, 40.0, 57):
         n = smooth_grid(L, 0.25, 48, 96)
-        assert 48 <= n <= 96 and n % 2 == 0 and _is_smooth(n)
+        assert 48 <= n <= 96 and _is_smooth(n)
         if n < 96:
             assert n >= L / 0.25 - 1e-9
             # the smallest such size
-            assert all(not (k % 2 == 0 and _is_smooth(k)) for k in range(max(48, math.ceil(L / 0.25 - 1e-9)), n))
+            assert all(not _is_smooth(k) for k in range(max(48, math.ceil(L / 0.25 - 1e-9)), n))
+    # the sizes the batched workload's clamp allows, odd ones included
+    sizes = {smooth_grid(L, 0.25, 48, 96) for L in np.linspace(11.0, 24.5, 2000)}
+    assert sizes == {48, 50, 54, 60, 64, 72, 75, 80, 81, 90, 96}
 
 
 def test_batched_snapshots_follow_the_recipe():
@@ -60,7 +63,7 @@ def test_serving_stream_is_seeded_and_sized():
     assert np.array_equal(t1, t2) and all(np.array_equal(a.pos, b.pos) for a, b in zip(c1, c2))
     assert np.all(np.diff(t1) > 0)
     for c in c1:
-        assert 8 <= c.n_ion <= 512 and 32 <= c.n <= 160 and _is_smooth(c.n) and c.n % 2 == 0
+        assert 8 <= c.n_ion <= 512 and 32 <= c.n <= 160 and _is_smooth(c.n)
 
 
 def test_md_inputs():
@@ -72,5 +75,5 @@ def test_md_inputs():
         assert np.allclose((mass[:, None] * v).sum(0), 0.0, atol=1e-12)
         assert np.array_equal(v, md_velocities(SEED_BASE + 7, mass, c.T))
         # the MD cells keep a hard core of 0.6 r_s, scaled with the density
-        assert _min_image_distance(c.pos, c.L) >= 0.6 * c.meta["rs"] and c.n % 2 == 0 and _is_smooth(c.n)
+        assert _min_image_distance(c.pos, c.L) >= 0.6 * c.meta["rs"] and _is_smooth(c.n)
         assert c.n >= c.L / (0.10 / 0.529177210903) - 1e-9        # 0.10 Angstrom or finer

@@ -61,10 +61,10 @@ def _is_smooth(k: int) -> bool:
 
 
 def smooth_grid(L: float, spacing: float, lo: int, hi: int) -> int:
-    """Smallest even 2,3,5-smooth n >= L/spacing, clamped to [lo, hi]."""
+    """Smallest 2,3,5-smooth n >= L/spacing (odd or even), clamped to [lo, hi]."""
     target = max(lo, int(math.ceil(L / spacing - 1e-9)))
     k = target
-    while not (k % 2 == 0 and _is_smooth(k)):
+    while not _is_smooth(k):
         k += 1
     return int(min(k, hi))
 
@@ -195,7 +195,7 @@ def hydrogen_md_cells() -> list[Cell]:
     """The three warm-dense-hydrogen MD systems whose time per MD step the
     paper tabulates (Methods, Table 2): 32 H at r_s = 1, 14 H at r_s = 2 and
     14 H at r_s = 3.23, all at theta = 1, on a 0.10 Angstrom grid (rounded up
-    to an even 2,3,5-smooth size), seeded random liquid-like positions."""
+    to a 2,3,5-smooth size), seeded random liquid-like positions."""
     out = []
     for i, (n_ion, rs) in enumerate(((32, 1.0), (14, 2.0), (14, 3.23))):
         L = (n_ion * 4.0 * math.pi * rs ** 3 / 3.0) ** (1.0 / 3.0)
