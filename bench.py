@@ -2,22 +2,30 @@
 """Benchmark of the OFDFT hot path on one GB300 (or N replicas under torchrun).
 
 Metric: converged OFDFT snapshots/s at 1e-6 Ha/atom (with functional evals/s
-and effective HBM GB/s alongside) on the single-instance workload: 64 H ions
-(Z = 1) at seeded random positions with a 0.8 bohr hard core, r_s = 2.0 bohr,
-theta = 1.0, 128^3 grid.  A step is one snapshot end to end: structure factor,
-local pseudopotential and Ewald energy (the per-snapshot setup), then L-BFGS
-from the uniform density to |dF|/ion < 1e-6 Ha for 3 iterations and residual
-< 1e-4 Ha.  The nonlocal kernel table (fixed by nbar and T) is built at plan
-creation, outside the timed region, as the paper excludes its kernel-table
-initialisation from its timings.
+and effective HBM GB/s alongside) on the largest single-GPU workload: 1024
+ions of Z = 3 at seeded random positions with a 0.8 bohr hard core, r_s = 2.5
+bohr, theta = 0.3, 256^3 grid, FP32 bulk arithmetic with FP64 sums and line
+search.  A step is one snapshot end to end: structure factor, local
+pseudopotential and Ewald energy (the per-snapshot setup), L-BFGS from the
+uniform density to |dF|/ion < 1e-6 Ha for 3 iterations and residual < 1e-4
+Ha, then the electron-ion structure factor S_ei on the first 200 |q| shells.
+The nonlocal kernel table (fixed by nbar and T) is built at plan creation,
+outside the timed region, as the paper excludes its kernel-table
+initialisation from its timings.  The inputs (1.7 GB of plan state) exceed
+the 126 MB L2; the L2 is flushed before every step all the same.
+
+Alongside: the 64-H r_s = 2 theta = 1 128^3 cell (FP32 and the FP64 plain
+path), the FP64 path on the 256^3 cell, the error of each against the
+oracle's converged minimum, the batched form (64 snapshots of 48^3-96^3), the
+serving form (2000 Poisson requests of 32^3-160^3) and MD time per step.
 
 Arms:
-  default           the CUDA library, FP32 bulk with FP64 sums and line search
-                    (the FP64 plain path is measured alongside as "fp64").
+  default           the CUDA library.
   --impl reference  the FP64 CPU oracle on the host cores, each step a bounded
-                    sample (per-snapshot setup + one functional evaluation),
-                    extrapolated to a snapshot with the oracle's own evaluation
-                    count for this cell.
+                    sample of the same snapshot (per-snapshot setup on a
+                    sample of the ions + one functional evaluation),
+                    extrapolated to a snapshot with the oracle's own
+                    evaluation count for this cell.
 Under torchrun (N > 1) every rank solves its own copy of the snapshot stream
 (replicas, no data-path collective); value = all ranks' snapshots / max time.
 """
@@ -38,10 +46,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "converged OFDFT snapshots/sec and functional evals/sec at 1e-6 Ha/atom; HBM GB/s"
-WORKLOAD = ("64 H ions (Z=1), r_s=2.0 bohr, theta=1.0, 128^3 grid, seeded random positions "
-            "(0.8 bohr hard core), Gaussian-smoothed Coulomb ions rc=1.0, L-BFGS m=8 from the uniform "
-            "density to 1e-6 Ha/atom and residual 1e-4 Ha")
+WORKLOAD = ("1024 Z=3 ions, r_s=2.5 bohr, theta=0.3, 256^3 grid, seeded random positions (0.8 bohr hard "
+            "core), Gaussian-smoothed Coulomb ions rc=1.0, L-BFGS m=8 from the uniform density to 1e-6 "
+            "Ha/atom and residual 1e-4 Ha, then S_ei on 200 |q| shells")
+HEADLINE_CFG = 4
+N_SHELLS = 200
 TOL_F, TOL_R = 1e-6, 1e-4
+
+
+def config_dict(world: int, snaps: int, cell=None) -> dict:
+    """The `config` object of both arms' JSON lines (same keys)."""
+    workload = WORKLOAD if cell is None or cell.label == "rand1024_Z3_rs2.5_n256" else \
+        f"{cell.label}: {cell.n_ion} ions, {cell.n}^3 grid, theta={cell.theta:g}, L-BFGS to 1e-6 Ha/atom, S_ei"
+    return {"workload": workload, "global_batch": snaps, "seq_len": None, "parallelism": f"replicas x{world}",
+            "l2": "flushed between steps (256 MB write outside the timed interval); the 256^3 cell's "
+                  "1.7 GB plan state exceeds the L2 as well"}
 
 
 def parse():
@@ -50,11 +69,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cell", type=int, default=HEADLINE_CFG, choices=[1, 2, 4],
+                    help="single-cell workload of a step: 4 = 1024 Z=3 ions on 256^3 (the headline), "
+                         "2 = 64 H on 128^3, 1 = the 4-ion fcc cell on 32^3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cfg2", action="store_true", help="skip the 128^3 single-cell block")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--serving", type=int, default=0,
-                    help="also run the serving loop on this many Poisson requests (0 = skip)")
+    ap.add_argument("--serving", type=int, default=2000,
+                    help="Poisson requests of the serving block (0 = skip)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-md", action="store_true", help="skip the MD time-per-step block")
     return ap.parse_args()
@@ -137,6 +160,32 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def golden_minima():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_minima.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def error_vs_oracle(cell, out, rho=None):
+    """|F - F_oracle| / N_ion against the oracle's converged minimum of the
+    same cell (tests/golden, written from oracle/ alone), and the relative L2
+    distance of the density where the oracle's density is stored."""
+    g = golden_minima().get(cell.label)
+    if not g:
+        return None
+    r = {"dF_per_ion": abs(out["F_total"] - g["energies"]["total"]) / cell.n_ion,
+         "oracle_tol_F_per_ion": g["tol_F_per_ion"], "oracle_tol_residual": g["tol_residual"]}
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_density_{cell.label}.npy")
+    if rho is not None and os.path.exists(path):
+        import numpy as np
+        ref = np.load(path).astype(np.float64).reshape(-1)
+        n = rho.double().cpu().numpy().reshape(-1)
+        r["density_rel_l2"] = float(np.linalg.norm(n - ref) / np.linalg.norm(ref))
+    return r
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -145,25 +194,27 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cell = config_cell(2)
+    cell = config_cell(args.cell)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
 
-    def make(precision):
-        plan = og.Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=precision)
+    def make(c, precision):
+        plan = og.Plan(c.L, c.n, c.Z, c.T, rc=c.rc, precision=precision)
         dt = torch.float32 if precision == "fp32" else torch.float64
-        rho = torch.empty(cell.n ** 3, dtype=dt, device=dev)
-        pos = torch.tensor(cell.pos, dtype=torch.float64, device=dev)
+        rho = torch.empty(c.n ** 3, dtype=dt, device=dev)
+        pos = torch.tensor(c.pos, dtype=torch.float64, device=dev)
         return plan, rho, pos
 
-    def step(plan, rho, pos):
+    def step(plan, rho, pos, shells=N_SHELLS):
         plan.structure_factor(pos)
         out = plan.minimize(rho, start_uniform=True, tol_F_per_ion=TOL_F, tol_residual=TOL_R)
         if not out["converged"]:
             raise RuntimeError(f"snapshot did not converge: {out}")
+        if shells:
+            out["sei"] = plan.sei_shells(rho, shells)
         return out
 
     def barrier():
@@ -172,7 +223,7 @@ def run_ours(args, rank, world, local):
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(plan, rho, pos, steps):
+    def timed(plan, rho, pos, steps, shells=N_SHELLS):
         """Per-step device time from CUDA events on the library's stream; L2
         flushed before every step, outside the timed interval."""
         total_ms, evals, iters, last = 0.0, 0, 0, None
@@ -181,7 +232,7 @@ def run_ours(args, rank, world, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            last = step(plan, rho, pos)
+            last = step(plan, rho, pos, shells)
             e1.record(stream)
             e1.synchronize()
             total_ms += e0.elapsed_time(e1)
@@ -194,11 +245,11 @@ def run_ours(args, rank, world, local):
         return mor(x, dev)
 
     res = {}
-    plan, rho, pos = make("fp32")
+    plan, rho, pos = make(cell, "fp32")
     for _ in range(args.warmup):
         step(plan, rho, pos)
     # the timed region: launches are counted, but no event pair is recorded
-    # around each launch (those pairs serialise the stream and cost ~15%)
+    # around each launch (those pairs serialise the stream)
     plan.profile_enable(False)
     barrier()
     with ClockSampler(local) as clk:
@@ -214,12 +265,13 @@ def run_ours(args, rank, world, local):
     barrier()
     prof = plan.profile_read()
     res["fp32"] = dict(total_ms=total_ms, total_ms_max=total_ms_max, evals=evals, iters=iters, last=last,
-                       prof=prof, counts=counts, profiled_ms=prof_ms, clocks=clk.summary())
+                       prof=prof, counts=counts, profiled_ms=prof_ms, clocks=clk.summary(),
+                       error=error_vs_oracle(cell, last, rho))
 
-    # end to end through the public API with host buffers: positions copied in,
-    # converged density and energies copied out, every step
+    # end to end through the public API with host buffers: positions copied in
+    # from pinned host memory; the converged density, the energies and S_ei
+    # copied out, every step
     plan.profile_enable(False)
-    # positions staged in pinned host memory, as a caller streaming snapshots would
     host_pos_t = torch.empty(tuple(cell.pos.shape), dtype=torch.float64, pin_memory=True)
     host_pos_t.copy_(torch.from_numpy(np.ascontiguousarray(cell.pos, dtype=np.float64)))
     host_pos = host_pos_t.numpy()
@@ -234,24 +286,27 @@ def run_ours(args, rank, world, local):
         t0 = time.perf_counter()
         plan.structure_factor(host_pos)
         out = plan.minimize(rho, start_uniform=True, tol_F_per_ion=TOL_F, tol_residual=TOL_R)
+        plan.sei_shells(rho, N_SHELLS)
         host_rho.copy_(rho, non_blocking=True)
         torch.cuda.synchronize(dev)
         e2e_s += time.perf_counter() - t0
         if not out["converged"]:
             raise RuntimeError("e2e snapshot did not converge")
     e2e_s = max_over_ranks(e2e_s)
-    res["e2e"] = dict(seconds=e2e_s, h2d=host_pos.nbytes, d2h=host_rho.numel() * 4 + 11 * 8)
-    plan_bytes = plan.lib.ofdft_plan_bytes
+    res["e2e"] = dict(seconds=e2e_s, h2d=host_pos.nbytes,
+                      d2h=host_rho.numel() * 4 + 11 * 8 + 2 * N_SHELLS * 8)
     plan.close()
 
     if not args.no_fp64:
-        p64, r64, pos64 = make("fp64")
-        step(p64, r64, pos64)
-        n64 = max(1, min(3, args.steps))
-        barrier()
-        ms64, ev64, it64, last64 = timed(p64, r64, pos64, n64)
-        res["fp64"] = dict(total_ms=max_over_ranks(ms64), evals=ev64, iters=it64, steps=n64, last=last64)
+        p64, r64, pos64 = make(cell, "fp64")
+        _, ev64, it64, last64 = timed(p64, r64, pos64, 1)       # warm-up step (plan set-up paths)
+        ms64, ev64, it64, last64 = timed(p64, r64, pos64, 1)
+        res["fp64"] = dict(total_ms=max_over_ranks(ms64), evals=ev64, iters=it64, steps=1, last=last64,
+                           error=error_vs_oracle(cell, last64, r64))
         p64.close()
+        del r64
+    if not args.no_cfg2:
+        res["cfg2"] = run_cfg2(args, dev, make, timed, max_over_ranks)
     if not args.no_batched:
         res["batched"] = run_batched(args, dev)
     if args.serving > 0:
@@ -262,6 +317,26 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.destroy_process_group()
     return cell, res
+
+
+def run_cfg2(args, dev, make, timed, max_over_ranks):
+    """The 64-H r_s = 2 theta = 1 cell on 128^3 (single snapshots, no S_ei):
+    FP32 bulk and the plain FP64 path, each against the oracle's minimum."""
+    from workloads import config_cell
+    cell = config_cell(2)
+    out = {"workload": "64 H ions (Z=1), r_s=2.0 bohr, theta=1.0, 128^3 grid, seeded random positions"}
+    for precision, steps in (("fp32", max(3, args.steps)), ("fp64", 3)):
+        if precision == "fp64" and args.no_fp64:
+            continue
+        plan, rho, pos = make(cell, precision)
+        timed(plan, rho, pos, 2, 0)
+        ms, ev, it, last = timed(plan, rho, pos, steps, 0)
+        ms = max_over_ranks(ms)
+        out[precision] = {"snapshots_per_s": steps / (ms * 1e-3), "evals_per_snapshot": ev / steps,
+                          "evals_per_sec": ev / (ms * 1e-3), "ms_per_snapshot": ms / steps,
+                          "error_vs_oracle": error_vs_oracle(cell, last, rho)}
+        plan.close()
+    return out
 
 
 def run_batched(args, dev):
@@ -352,23 +427,28 @@ def run_md(args, dev, warm=10, steps=50):
 
 
 def run_serving(args, dev):
-    """Poisson request stream (8-512 ions, 32^3-160^3): sequential service rate
-    first, then the continuous-batching server at 0.5, 0.9 and 1.5 times it."""
+    """Poisson request stream (8-512 ions, 32^3-160^3): the plain sequential
+    service rate on a sample of the stream first (every 10th request, at most
+    200), then the continuous-batching server on the whole stream at 0.5, 0.9
+    and 1.5 times that rate."""
     import numpy as np
     from paper_2601_23002_gb300.serving import Server, run_sequential, summarize
     from workloads import serving_requests
     _, cells = serving_requests(args.serving)
     srv = Server(slots=16, precision="fp32")
     srv.prepare(cells)
-    n_seq = min(len(cells), 40)
-    _, t_seq = run_sequential(cells[:n_seq])
-    mu = n_seq / t_seq
-    out = {"requests": len(cells), "sequential_snapshots_per_s": mu, "slots": 16}
+    sample = cells[::10][:200]
+    seq, t_seq = run_sequential(sample)
+    mu = len(sample) / t_seq
+    out = {"requests": len(cells), "sequential_snapshots_per_s": mu, "sequential_sample": len(sample),
+           "sequential_converged": sum(1 for r in seq if r["converged"]), "slots": 16,
+           "grids": sorted(set(c.n for c in cells))}
     for rho_f in (0.5, 0.9, 1.5):
         rng = np.random.default_rng(7)
         arrivals = np.cumsum(rng.exponential(1.0 / (rho_f * mu), size=len(cells)))
         done = srv.run(arrivals, cells)
         out[f"load_{rho_f}"] = summarize(done, srv.wall)
+    out["served_over_sequential_at_1.5"] = out["load_1.5"]["snapshots_per_s"] / mu
     return out
 
 
@@ -410,47 +490,88 @@ def roofline(prof):
 
 
 # --------------------------------------------------------------- the oracle
-def oracle_sample(cell, n_evals: int):
-    """Oracle per-snapshot setup (local pseudopotential, Ewald) and n_evals
-    functional evaluations at a perturbed density; returns seconds each."""
+_ORACLE_PLANS = {}
+
+
+def oracle_sample(cell, n_evals: int, k_sf: int = 8, k_ew: int = 128):
+    """The oracle's per-snapshot work, timed on a bounded sample: the ion
+    structure factor (which V_loc is built from) on k_sf ions scaled by
+    N_ion / k_sf (linear in the ions), the Ewald energy on k_ew ions scaled by
+    (N_ion / k_ew)^2 (its pair sum), and n_evals FP64 functional evaluations
+    at a perturbed density.  The evaluations run on a copy of the cell with
+    k_sf ions of charge N_e / k_sf (the same N_e, nbar, T, L and grid: an
+    evaluation's cost does not depend on the ions).  Returns seconds:
+    (kernel-table set-up, per-snapshot set-up, per evaluation)."""
     import numpy as np
     from oracle.functional import Functional
-    from oracle.cell import vloc_g, ewald_energy
+    from oracle.cell import structure_factor, ewald_energy
+    from workloads.cells import Cell
+    ni = cell.n_ion
+    k_sf, k_ew = min(k_sf, ni), min(k_ew, ni)
+    key = (cell.label, k_sf)
+    if key not in _ORACLE_PLANS:                   # the kernel table: built once, like a plan
+        sub = Cell(L=cell.L, n=cell.n, Z=np.full(k_sf, cell.n_electrons / k_sf), pos=cell.pos[:k_sf],
+                   theta=cell.theta, rc=cell.rc)
+        t0 = time.perf_counter()
+        _ORACLE_PLANS[key] = (Functional(sub), time.perf_counter() - t0)
+    F, t_plan = _ORACLE_PLANS[key]
     t0 = time.perf_counter()
-    F = Functional(cell)                           # includes the kernel table
-    t_plan = time.perf_counter() - t0
+    structure_factor(cell.pos[:k_sf], cell.n, cell.L)
+    t_sf = (time.perf_counter() - t0) * ni / k_sf
     t0 = time.perf_counter()
-    vloc_g(cell.Z, cell.pos, cell.n, cell.L, cell.rc)
-    ewald_energy(cell.Z, cell.pos, cell.L)
-    t_snap = time.perf_counter() - t0
+    ewald_energy(np.asarray(cell.Z[:k_ew], float), cell.pos[:k_ew], cell.L)
+    t_ew = (time.perf_counter() - t0) * (ni / k_ew) ** 2
     rng = np.random.default_rng(0)
     psi = math.sqrt(F.nbar) * (1 + 0.05 * rng.standard_normal((cell.n,) * 3))
     t0 = time.perf_counter()
     for _ in range(n_evals):
         F.evaluate_psi(psi)
     t_eval = (time.perf_counter() - t0) / n_evals
-    return t_plan, t_snap, t_eval
+    return t_plan, t_sf + t_ew, t_eval
 
 
 def oracle_evals_per_snapshot(label: str):
-    try:
-        with open(os.path.join(ROOT, "tests", "golden", "oracle_minima.json")) as f:
-            g = json.load(f)
-        return int(g[label]["evaluations"]), "oracle's own count (tests/golden/oracle_minima.json)"
-    except Exception:
-        return None, None
+    """(plain L-BFGS count, preconditioned count) of the oracle's converged
+    minimum of this cell, from tests/golden/oracle_minima.json (None where
+    absent)."""
+    g = golden_minima()
+    plain = g.get(label)
+    pre = g.get(label + "_precond") or (plain if plain and plain.get("preconditioned") else None)
+    if plain and plain.get("preconditioned"):
+        plain = None
+    return (int(plain["evaluations"]) if plain else None), (int(pre["evaluations"]) if pre else None)
 
 
-def cpu_baseline(cell, fallback_evals: int, n_evals: int = 2):
+def cpu_baseline(cell, fallback_evals: int, n_evals: int = 1):
     t_plan, t_snap, t_eval = oracle_sample(cell, n_evals)
-    ev, src = oracle_evals_per_snapshot(cell.label)
-    if ev is None:
-        ev, src = fallback_evals, "evaluation count of the FP64 GPU run of the same snapshot"
+    ev_plain, ev_pre = oracle_evals_per_snapshot(cell.label)
+    ev = ev_plain or ev_pre or fallback_evals
+    src = ("the plain oracle's own count" if ev_plain else
+           "the preconditioned oracle's own count (a plain run takes hours)" if ev_pre else
+           "the FP64 GPU run's count (no oracle count stored)")
     per_snap = t_snap + ev * t_eval
-    return {"value": 1.0 / per_snap, "unit": "snapshots/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle per-snapshot setup ({t_snap:.2f} s) + {n_evals} FP64 functional evaluations of "
-                       f"the 128^3 cell ({t_eval:.2f} s each), extrapolated with {ev} evaluations per converged "
-                       f"snapshot ({src}); kernel-table setup {t_plan:.2f} s excluded as on the GPU side")}
+    out = {"value": 1.0 / per_snap, "unit": "snapshots/s", "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": (f"oracle per-snapshot setup ({t_snap:.1f} s: structure factor on 8 ions x N_ion/8, "
+                      f"Ewald on 128 ions x (N_ion/128)^2) + {n_evals} FP64 functional evaluation(s) of the "
+                      f"{cell.n}^3 cell ({t_eval:.2f} s each), extrapolated with {ev} evaluations per converged "
+                      f"snapshot ({src}, tests/golden/oracle_minima.json); kernel-table setup {t_plan:.1f} s "
+                      f"excluded as on the GPU side")}
+    if ev_plain and ev_pre:
+        out["value_preconditioned"] = 1.0 / (t_snap + ev_pre * t_eval)
+        out["evaluations_plain_preconditioned"] = [ev_plain, ev_pre]
+    return out
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # -------------------------------------------------------------------- main
@@ -461,9 +582,12 @@ def main():
         if rank != 0:
             return 0
         from workloads import config_cell
-        cell = config_cell(2)
-        ev, src = oracle_evals_per_snapshot(cell.label)
-        ev = ev or 100
+        cell = config_cell(args.cell)
+        ev_plain, ev_pre = oracle_evals_per_snapshot(cell.label)
+        ev = ev_plain or ev_pre or 100
+        # each step: the bounded sample of oracle_sample (per-snapshot setup
+        # on a sample of the ions + one FP64 evaluation), extrapolated to a
+        # snapshot with the oracle's own evaluation count
         for _ in range(args.warmup):
             oracle_sample(cell, 1)
         per = []
@@ -471,13 +595,15 @@ def main():
             _, t_snap, t_eval = oracle_sample(cell, 1)
             per.append(t_snap + ev * t_eval)
         value = len(per) / sum(per)
+        sample = (f"per step: oracle per-snapshot setup (structure factor on 8 ions x N_ion/8, Ewald on 128 "
+                  f"ions x (N_ion/128)^2) + 1 FP64 evaluation of the {cell.n}^3 cell, extrapolated with {ev} "
+                  f"evaluations per snapshot (the {'plain' if ev_plain else 'preconditioned'} oracle's own count)")
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "snapshots/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(per) / len(per),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "host cores"},
-                "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
-                                 "sample": f"per step: oracle per-snapshot setup + 1 FP64 evaluation of the "
-                                           f"128^3 cell, extrapolated with {ev} evaluations per snapshot ({src})"},
+                "data": "synthetic", "config": config_dict(world, world * args.steps, cell),
+                "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "cpu_model": cpu_model(),
+                                 "value": value, "sample": sample},
                 "e2e": {"value": value, "unit": "snapshots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
@@ -498,13 +624,13 @@ def main():
         "metric": METRIC, "value": value, "unit": "snapshots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r32["total_ms_max"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 sums and line search)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": snaps, "seq_len": None, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between steps (256 MB write outside the timed interval)"},
+        "config": config_dict(world, snaps, cell),
         "evals_per_sec": evals_per_s, "evals_per_snapshot": r32["evals"] / args.steps,
         "iterations_per_snapshot": r32["iters"] / args.steps,
         "effective_hbm_gbs": evals_per_s / world * b_eval / 1e9,
         "effective_hbm_note": "14 N w bytes per evaluation (w = 4) x evals/s, per GPU",
         "final_energy": {k: r32["last"][k] for k in ("F_total", "residual", "N_e")},
+        "error_vs_oracle": r32["error"],
         "clocks": r32["clocks"],
         "e2e": {"value": snaps / res["e2e"]["seconds"], "unit": "snapshots/s",
                 "h2d_bytes_per_step": res["e2e"]["h2d"], "d2h_bytes_per_step": res["e2e"]["d2h"]},
@@ -520,7 +646,10 @@ def main():
         line["fp64"] = {"value": world * r["steps"] / (r["total_ms"] * 1e-3), "unit": "snapshots/s",
                         "evals_per_sec": world * r["evals"] / (r["total_ms"] * 1e-3),
                         "evals_per_snapshot": r["evals"] / r["steps"], "steps": r["steps"],
-                        "F_total": r["last"]["F_total"]}
+                        "F_total": r["last"]["F_total"], "error_vs_oracle": r["error"],
+                        "fp32_minus_fp64_F_per_ion": (r32["last"]["F_total"] - r["last"]["F_total"]) / cell.n_ion}
+    if "cfg2" in res:
+        line["cfg2"] = res["cfg2"]
     if "batched" in res:
         line["batched"] = res["batched"]
     if "serving" in res:

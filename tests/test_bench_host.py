@@ -92,8 +92,9 @@ def _run_bench(args, env_extra=None):
 
 
 def test_reference_arm_prints_one_complete_line():
-    # the oracle on the host cores, one bounded sample per step
-    p = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1"])
+    # the oracle on the host cores, one bounded sample per step (on the 32^3
+    # fcc cell here, to keep the CPU suite short; the default is the 256^3 cell)
+    p = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1", "--cell", "1"])
     assert p.returncode == 0, p.stderr[-2000:]
     lines = [l for l in p.stdout.splitlines() if l.strip()]
     d = json.loads(lines[-1])
@@ -104,9 +105,13 @@ def test_reference_arm_prints_one_complete_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the same config keys as the CUDA arm's line
+    from workloads import config_cell
+    assert d["config"] == bench.config_dict(1, 1, config_cell(1))
+    assert set(d["config"]) == set(bench.config_dict(1, 1))
 
 
 def test_reference_arm_runs_on_rank_0_only():
-    p = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1"],
+    p = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1", "--cell", "1"],
                    {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert p.returncode == 0 and p.stdout.strip() == ""
