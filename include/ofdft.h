@@ -83,6 +83,12 @@ typedef struct {
     int precision;       /* ofdft_precision                                            */
     int terms;           /* OFDFT_TERM_* mask                                          */
     double alpha;        /* exponent a of E_NL = int int n^a K n^a (0 < a < 1)         */
+    int fd64;            /* FP32 plans: 1 inverts the Fermi-Dirac integral (eta and
+                            I_3/2 / I_1/2 of the finite-T Thomas-Fermi term, Eq. 1) in
+                            FP64 at every grid point, from the density value as stored;
+                            0 (default) uses the FP32 fit.  FP64 plans always use FP64.
+                            The FP64 inversion runs on the FP64 pipe and costs about
+                            as much as the rest of an evaluation at 256^3.            */
 } ofdft_opts;
 
 /* Energies in Ha (per cell) and derived scalars. */
@@ -113,7 +119,7 @@ typedef struct {
 
 typedef struct ofdft_plan ofdft_plan;
 
-/* Defaults: FP64, all terms, alpha = 1/2; tol 1e-6 Ha/ion, residual 1e-4 Ha,
+/* Defaults: FP64, all terms, alpha = 1/2, fd64 = 0; tol 1e-6 Ha/ion, residual 1e-4 Ha,
  * m = 8, max_iter = 1000, c1 = 1e-4, c2 = 0.9. */
 void ofdft_default_opts(ofdft_opts* opts);
 void ofdft_default_min_opts(ofdft_min_opts* opts);

@@ -29,7 +29,8 @@ class Cell(ctypes.Structure):
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("terms", ctypes.c_int), ("alpha", ctypes.c_double)]
+    _fields_ = [("precision", ctypes.c_int), ("terms", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("fd64", ctypes.c_int)]
 
 
 class Energies(ctypes.Structure):

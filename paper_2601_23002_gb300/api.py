@@ -34,12 +34,13 @@ class Plan:
     """One cell: L (bohr), n, Z[n_ion], rc (bohr), T (Ha)."""
 
     def __init__(self, L: float, n: int, Z, T: float, rc: float = 1.0, precision: str = "fp64",
-                 terms: int = C.TERMS_ALL, alpha: float = 0.5, stream=None):
+                 terms: int = C.TERMS_ALL, alpha: float = 0.5, stream=None, fd64: bool = False):
         self.lib = C.load()
         self._Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64))
         self.cell = C.Cell(float(L), int(n), int(self._Z.size),
                            self._Z.ctypes.data_as(C.c_double_p), float(rc), float(T))
-        self.opts = C.Opts(C.OFDFT_FP32 if precision == "fp32" else C.OFDFT_FP64, int(terms), float(alpha))
+        self.opts = C.Opts(C.OFDFT_FP32 if precision == "fp32" else C.OFDFT_FP64, int(terms), float(alpha),
+                           int(bool(fd64)))
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.n = int(n)
         self.stream = stream
@@ -272,11 +273,12 @@ def minimize(cell, rho: torch.Tensor | None = None, precision: str = "fp64", dev
     return out, res
 
 
-def plan_for_cell(cell, precision="fp64", terms=C.TERMS_ALL, alpha=0.5, stream=None) -> Plan:
+def plan_for_cell(cell, precision="fp64", terms=C.TERMS_ALL, alpha=0.5, stream=None, fd64=False) -> Plan:
     """Plan + structure factor for a workloads.Cell (or any object with
-    L, n, Z, pos, rc, T)."""
+    L, n, Z, pos, rc, T).  fd64: FP32 plans invert the Fermi-Dirac integral
+    in FP64 (ofdft_opts.fd64)."""
     p = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=precision, terms=terms, alpha=alpha,
-             stream=stream)
+             stream=stream, fd64=fd64)
     try:
         p.structure_factor(cell.pos)
     except BaseException:

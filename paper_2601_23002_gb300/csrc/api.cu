@@ -107,6 +107,7 @@ static int validate(const ofdft_cell* c, const ofdft_opts* o) {
   if (o->precision != OFDFT_FP64 && o->precision != OFDFT_FP32) { set_error("bad precision"); return OFDFT_ERR_INVALID; }
   if (o->terms < 0 || o->terms > OFDFT_TERMS_ALL) { set_error("bad terms mask"); return OFDFT_ERR_INVALID; }
   if (!(o->alpha > 0 && o->alpha < 1)) { set_error("alpha must be in (0, 1)"); return OFDFT_ERR_INVALID; }
+  if (o->fd64 != 0 && o->fd64 != 1) { set_error("fd64 must be 0 or 1"); return OFDFT_ERR_INVALID; }
   return OFDFT_OK;
 }
 
@@ -126,7 +127,7 @@ static int validate_min_opts(const ofdft_min_opts& o, const char* who) {
 static CellSpec spec_of(const ofdft_cell* c, const ofdft_opts* o) {
   CellSpec s;
   s.L = c->L; s.n = c->n; s.Z.assign(c->Z, c->Z + c->n_ion); s.rc = c->rc; s.T = c->T;
-  s.terms = o->terms; s.alpha = o->alpha;
+  s.terms = o->terms; s.alpha = o->alpha; s.fd64 = o->fd64 != 0;
   return s;
 }
 
@@ -137,6 +138,7 @@ void ofdft_default_opts(ofdft_opts* o) {
   o->precision = OFDFT_FP64;
   o->terms = OFDFT_TERMS_ALL;
   o->alpha = 0.5;
+  o->fd64 = 0;
 }
 
 void ofdft_default_min_opts(ofdft_min_opts* o) {

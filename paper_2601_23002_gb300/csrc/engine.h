@@ -17,6 +17,7 @@ struct CellSpec {
   double T;
   int terms;
   double alpha;
+  bool fd64 = false;   // FP32 plans: FP64 Fermi-Dirac inversion per point
 };
 
 class IEngine {

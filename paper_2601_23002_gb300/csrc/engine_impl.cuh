@@ -6,7 +6,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "engine.h"
@@ -16,6 +19,7 @@
 #include "plane.cuh"
 #include "setup.cuh"
 #include "vecops.cuh"
+#include "zpass256.cuh"
 
 namespace ofdft {
 
@@ -87,6 +91,9 @@ class Engine : public IEngine {
   // launch geometry
   int zR = 0, zP = 0, yJ = 0, xJ = 0;
   size_t smem_zf = 0, smem_zi = 0, smem_y = 0, smem_x = 0, smem_xp = 0;
+  // n = 256, FP32, tiled path: the z passes with register transforms (zpass256.cuh)
+  bool z256 = false, z256_allowed = true;
+  size_t smem_zf256 = 0, smem_zi256 = 0;
   int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_stream = 0, nsm = 152;
   // device memory
   std::vector<void*> allocs;
@@ -172,6 +179,8 @@ class Engine : public IEngine {
     tune.zR = env("OFDFT_ZR");
     const char* pe = std::getenv("OFDFT_PLANE");
     plane_allowed = !(pe && pe[0] == '0');
+    const char* z2 = std::getenv("OFDFT_Z256");
+    z256_allowed = !(z2 && z2[0] == '0');
     const char* p2 = std::getenv("OFDFT_PREC2");
     prec2_allowed = !(p2 && p2[0] == '0');
     tune.yJ = env("OFDFT_YJ");
@@ -284,6 +293,10 @@ class Engine : public IEngine {
     smem_pl = std::max(((size_t)n * (n + 1) + n) * sizeof(C) + (size_t)n * sizeof(int),
                        tree_scratch_bytes<T>(4, kPlaneThreads));
     planes = plane_allowed && smem_pl <= (size_t)225 * 1024;
+    // (rows per block even and dividing n^2: 8, 16 or 32)
+    z256 = z256_allowed && sizeof(T) == 4 && n == 256 && !planes && (zR == 8 || zR == 16 || zR == 32);
+    smem_zf256 = z256_fwd_bytes<T>(zR);
+    smem_zi256 = std::max(z256_inv_bytes<T>(zR, spectra().nact), tree_scratch_bytes<T>(12, kThreads));
     // clusters only for large grids: below n = 112 the snapshots that are
     // solved side by side (batched, served) fill the GPU anyway, and a
     // cluster launch waits for pairs of free SMs (64 cells of 48^3-96^3:
@@ -303,7 +316,7 @@ class Engine : public IEngine {
     size_t b = 0;
     b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
     if (planes) b += NH * sizeof(C);                         // vloc in plane order
-    b += (6 + 3 * (size_t)m_max) * Nv * sizeof(T);           // psi d g gp, P g x2, history s y P y
+    b += (6 + 3 * (size_t)m_max) * ((Nv * sizeof(T) + 255) / 256 * 256);   // psi d g gp, P g x2, history s y P y
     b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
     b += (size_t)(n + h) * sizeof(C);
     return b;
@@ -388,13 +401,18 @@ class Engine : public IEngine {
       if (planes && (rc = alloc(&vloc_pl, NH))) return rc;
     }
     {
+      // the minimiser's 6 + 3 m vectors in one allocation (slices on
+      // 256-byte boundaries): one cudaMalloc instead of thirty per plan
       T** vecs[6] = {&psi, &d, &g, &gp, &pgv[0], &pgv[1]};
-      for (T** v : vecs)
-        if ((rc = alloc(v, Nv))) return rc;
+      const size_t slice = (Nv * sizeof(T) + 255) / 256 * 256 / sizeof(T);
+      T* arena = nullptr;
+      if ((rc = alloc(&arena, slice * (6 + 3 * (size_t)m_max)))) return rc;
+      size_t k = 0;
+      for (T** v : vecs) *v = arena + slice * k++;
       for (int i = 0; i < m_max; ++i) {
-        if ((rc = alloc(&Sh[i], Nv))) return rc;
-        if ((rc = alloc(&Yh[i], Nv))) return rc;
-        if ((rc = alloc(&PYh[i], Nv))) return rc;
+        Sh[i] = arena + slice * k++;
+        Yh[i] = arena + slice * k++;
+        PYh[i] = arena + slice * k++;
       }
       if (Nv > N) {
         // zero padding: the grid kernels write [0, N) only, the streaming
@@ -504,12 +522,18 @@ class Engine : public IEngine {
     }
     {
       const double tp2 = (2.0 * kPi / L) * (2.0 * kPi / L);
+      // entries per (kx, ky) row: kz = 0 .. kz_max with kz^2 <= g2cut/tp2 - mx^2 - my^2
       n_vloc = 0;
+      const double lim = g2cut_loc / tp2;
       for (int kx = 0; kx < n; ++kx)
         for (int ky = 0; ky < n; ++ky) {
           const int mx = kx <= (n - 1) / 2 ? kx : kx - n, my = ky <= (n - 1) / 2 ? ky : ky - n;
-          for (int kz = 0; kz < nh; ++kz)
-            if (tp2 * (double)(mx * mx + my * my + kz * kz) <= g2cut_loc) ++n_vloc;
+          const double r = lim - (double)(mx * mx + my * my);
+          if (r < 0) continue;
+          int kzm = (int)std::sqrt(r);
+          while (kzm + 1 < nh && (double)(kzm + 1) * (kzm + 1) <= r) ++kzm;
+          while (kzm >= 0 && (double)kzm * kzm > r) --kzm;
+          n_vloc += (size_t)std::min(kzm, nh - 1) + 1;
         }
     }
     OFDFT_CK(cudaStreamSynchronize(st));
@@ -540,18 +564,27 @@ class Engine : public IEngine {
     int dev = 0, lim = 0;
     OFDFT_CK(cudaGetDevice(&dev));
     OFDFT_CK(cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    // dynamic limit = opt-in maximum minus the kernel's own static shared memory
+    // dynamic limit = opt-in maximum minus the kernel's own static shared
+    // memory; set once per (device, kernel) for the process (plan creation
+    // stays cheap for the serving loop), after checking this plan's need
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
     auto raise = [&](const void* f, size_t need) -> int {
+      std::lock_guard<std::mutex> lock(mu);
       cudaFuncAttributes fa;
       OFDFT_CK(cudaFuncGetAttributes(&fa, f));
       const int dyn = lim - (int)fa.sharedSizeBytes;
       if (dyn < (int)need) { set_error("grid too large for shared memory"); return OFDFT_ERR_INVALID; }
+      if (done.count({dev, f})) return OFDFT_OK;
       OFDFT_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+      done.insert({dev, f});
       return OFDFT_OK;
     };
     int rc;
     if ((rc = raise((const void*)k_zfwd<T>, smem_zf))) return rc;
     if ((rc = raise((const void*)k_zinv_epi<T>, smem_zi))) return rc;
+    if (z256 && (rc = raise((const void*)k_zfwd256<T>, smem_zf256))) return rc;
+    if (z256 && (rc = raise((const void*)k_zinv256<T>, smem_zi256))) return rc;
     if ((rc = raise((const void*)k_ypass<T, -1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
@@ -717,7 +750,9 @@ class Engine : public IEngine {
                 pt};
     int g_rows = 0;                       // rows of G-space partials [g_rows][4]
     if (sp.nact > 0) {
-      OFDFT_RUN("k_zfwd", st, (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+      const double zb = (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C);
+      if (z256) OFDFT_RUN("k_zfwd256", st, zb, k_zfwd256<T><<<grid_z, kThreads, smem_zf256, st>>>(pa, sp, tw_h, tw_n, zR));
+      else OFDFT_RUN("k_zfwd", st, zb, k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
       if (planes) {
         OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), plane_kern<<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
         g_rows = nh * sp.nact;
@@ -734,8 +769,10 @@ class Engine : public IEngine {
     FinArgs<T> fa{pt, g_rows, pe, grid_z, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
     EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
-                  counters + 0, nullptr, nullptr, dsc};
-    OFDFT_RUN("k_zinv_epi", st, (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+                  counters + 0, nullptr, nullptr, dsc, cs.fd64 ? 1 : 0, cy};
+    const double eb = (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0);
+    if (z256) OFDFT_RUN("k_zinv256", st, eb, k_zinv256<T><<<grid_z, kThreads, smem_zi256, st>>>(sp, ea, tw_h, tw_n, zR));
+    else OFDFT_RUN("k_zinv_epi", st, eb, k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaStreamSynchronize(st));
@@ -756,7 +793,8 @@ class Engine : public IEngine {
     GArgs<T> ga{nullptr, Kt, (T)(tp * tp), (T)Omega, (T)(0.5 * Omega), (T)(1.0 / (double)N), (T)g2cut_loc, 0, pt,
                 precT};
     const double fb = 2.0 * NH * sizeof(C);
-    OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+    if (z256) OFDFT_RUN("k_zfwd256", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd256<T><<<grid_z, kThreads, smem_zf256, st>>>(pa, sp, tw_h, tw_n, zR));
+    else OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
     if (prec2) {
       // one field: two blocks (a cluster) per kz plane
       OFDFT_RUN("k_plane_prec2", st, fb, prec2_kern<<<dim3(2 * nh), kPlaneThreads, smem_pl2, st>>>(sp, ga, pn, rev_d, tw_n));
@@ -771,7 +809,9 @@ class Engine : public IEngine {
     FinArgs<T> fa{pt, 0, pe, 0, res_d};
     EpiArgs<T> ea{3, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)Te, (T)1, (T)0, cs.terms, out, pe, fa,
                   counters + 0, pold, pyout};
-    OFDFT_RUN("k_zinv_epi", st, (double)NH * sizeof(C) + (double)N * sizeof(T) * (pyout ? 3.0 : 1.0), k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+    const double pb = (double)NH * sizeof(C) + (double)N * sizeof(T) * (pyout ? 3.0 : 1.0);
+    if (z256) OFDFT_RUN("k_zinv256", st, pb, k_zinv256<T><<<grid_z, kThreads, smem_zi256, st>>>(sp, ea, tw_h, tw_n, zR));
+    else OFDFT_RUN("k_zinv_epi", st, pb, k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     return OFDFT_OK;
   }
 
@@ -1409,7 +1449,7 @@ int Engine<T>::pressure(const void* rho, double* p_out_h, void* stream_) {
   OFDFT_RUN("k_xpass", st, 4.0 * NH * sizeof(C), k_xpass<T, -1><<<dim3(grid_x, 2), kThreads, smem_xp, st>>>(sp, pn, tw_n, n, xJ));
   const int gb = 4 * nsm;
   const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
-  OFDFT_RUN("k_pressure_r", st, (double)N * sizeof(T), k_pressure_r<T><<<gb, 256, 0, st>>>((const T*)rho, N, (T)cy, (T)Te, cs.terms, partials));
+  OFDFT_RUN("k_pressure_r", st, (double)N * sizeof(T), k_pressure_r<T><<<gb, 256, 0, st>>>((const T*)rho, N, (T)cy, (T)Te, cs.terms, partials, cs.fd64 ? 1 : 0, cy));
   if ((rc = sum_partials(gb, 2, 0, st))) return rc;
   const double tp = 2.0 * kPi / L;
   const C* vl = (cs.terms & OFDFT_TERM_LOC) ? vloc : nullptr;

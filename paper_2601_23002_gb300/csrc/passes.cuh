@@ -592,6 +592,82 @@ template <typename T> struct EpiArgs {
   const T* pold;
   T* pyout;
   const double* dsc;     // when set, scale = dsc[0] and t = dsc[2] (a trial formed on the device)
+  int fd64;              // FP32 plans: invert the Fermi-Dirac integral in FP64 (y = cy_d n in FP64)
+  double cy_d;           // pi^2 / (sqrt2 T^(3/2)) in FP64, for fd64
+};
+
+// The pointwise functional at one grid point, shared by the z-pass epilogue
+// kernels: from the point's density (mode 0) or psi and d (mode 1) and the
+// inverse transforms of the active fields there (Hartree + local potential,
+// the n^a field, the psi field), the Thomas-Fermi and XC energy densities, the
+// potential (mode 0) or g' (mode 1) written to out[at], and the block's
+// partial sums acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2,
+// 5 int g' psi_t, 6 int n, 7 nonfinite count.
+template <typename T> struct EpiPoint {
+  bool has_n, has_na, has_psi, merged;
+  T Te, cy, alpha, nmin, tstep, tscale, muref;
+  __device__ __forceinline__ EpiPoint(const Spectra<T>& sp, const EpiArgs<T>& a)
+      : has_n(sp.s[0] != nullptr), has_na(sp.s[1] != nullptr), has_psi(sp.s[2] != nullptr),
+        merged(sp.merged != 0), Te(a.T_e), cy(a.cy), alpha(a.alpha), nmin((T)kNmin),
+        tstep(a.dsc ? (T)a.dsc[2] : a.t), tscale(a.dsc ? (T)a.dsc[0] : a.scale), muref(a.mu_ref) {}
+  __device__ __forceinline__ void point(const EpiArgs<T>& a, T pv, T dq, T hv, T kv, T lv, size_t at,
+                                        AccShort<T> (&acc)[8]) const {
+    T psit, nval;
+    if (a.mode == 0) {
+      nval = pv;
+      psit = sqrt(fmax(nval, (T)0));
+    } else {
+      psit = pv + tstep * dq;
+      nval = tscale * psit * psit;
+    }
+    const T nf = fmax(nval, nmin);
+    T vrest = 0;
+    if (a.terms & 1) {              // TF
+      if (sizeof(T) == 4 && a.fd64) {
+        // FP64 inversion from the stored density value; f_TF formed in FP64
+        double eta, p;
+        fd_eta_p((double)nf * a.cy_d, eta, p);
+        const double te = (double)Te;
+        vrest += (T)(te * eta);
+        acc[0].add((T)((double)nf * te * (eta - p)));
+      } else {
+        T eta, p;
+        fd_eta_p(nf * cy, eta, p);
+        vrest += Te * eta;
+        acc[0].add(nf * Te * (eta - p));
+      }
+    }
+    if (a.terms & 8) {              // XC
+      T exc, vxc;
+      pz81<T>(nf, exc, vxc);
+      vrest += vxc;
+      acc[1].add(nval * exc);
+    }
+    if (has_n) vrest += hv;
+    if (has_na) vrest += (T)2 * alpha * pow_t<T>(nf, alpha - (T)1) * kv;
+    // psi field: -lap(psi), or W = IFFT[(K + G^2/2) psi~] when merged
+    const T lw = has_psi ? lv : (T)0;
+    const T extra = merged ? lw : (T)0.5 * lw;     // psi v_NL + (-lap psi)/2 when merged
+    acc[2].add(vrest * nval);
+    acc[6].add(nval);
+    // g' = psi (v_rest - mu_ref) + lap/2: near convergence mu_ref is close to
+    // mu, so the projection g = 2 scale (g' - (mu - mu_ref) psi) cancels little
+    const T gp = psit * (vrest - muref) + extra;
+    T* __restrict__ gout = a.out;
+    if (a.mode == 0) {
+      const T phi = fmax(psit, (T)kPhiMin);
+      const T v = vrest + extra / phi;
+      if (gout) gout[at] = v;
+      // residual pieces with psi = sqrt(rho), scale 1: g' = psi v_rest + lap/2
+      if (!isfinite(v)) acc[7].add((T)1);
+    } else {
+      if (gout) gout[at] = gp;
+      acc[3].add(gp * dq);
+      if (!isfinite(gp)) acc[7].add((T)1);
+    }
+    acc[4].add(gp * gp);
+    acc[5].add(gp * psit);
+  }
 };
 
 // smem: stg[nact][R][nh] (complex; field f's real rows overwrite its own
@@ -720,67 +796,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_zinv_epi(Spectr
     }
     return;
   }
-  const bool has_n = sp.s[0] != nullptr, has_na = sp.s[1] != nullptr, has_psi = sp.s[2] != nullptr;
   const T* fH = realf[0];
   const T* fK = realf[1];
   const T* fL = realf[2];
-  const T Te = a.T_e;
-  const T cy = a.cy;
-  const T alpha = a.alpha, nmin = (T)kNmin;
-  const T tstep = a.dsc ? (T)a.dsc[2] : a.t, tscale = a.dsc ? (T)a.dsc[0] : a.scale, muref = a.mu_ref;
+  const EpiPoint<T> ep(sp, a);
   AccShort<T> acc[8];
-  // acc: 0 F_TF, 1 E_xc, 2 int v_rest n, 3 int g' d, 4 int g'^2, 5 int g' psi_t, 6 int n, 7 nonfinite
   const T* pd = pin + (size_t)Rfull * n;
-  T* __restrict__ gout = a.out;
-  for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-    const T pv = pin[q];
-    const T dq = a.mode != 0 ? pd[q] : (T)0;
-    T psit, nval;
-    if (a.mode == 0) {
-      nval = pv;
-      psit = sqrt(fmax(nval, (T)0));
-    } else {
-      psit = pv + tstep * dq;
-      nval = tscale * psit * psit;
-    }
-    const T nf = fmax(nval, nmin);
-    T vrest = 0;
-    if (a.terms & 1) {              // TF
-      T eta, p;
-      fd_eta_p(nf * cy, eta, p);
-      vrest += Te * eta;
-      acc[0].add(nf * Te * (eta - p));
-    }
-    if (a.terms & 8) {              // XC
-      T exc, vxc;
-      pz81<T>(nf, exc, vxc);
-      vrest += vxc;
-      acc[1].add(nval * exc);
-    }
-    if (has_n) vrest += fH[q];
-    if (has_na) vrest += (T)2 * alpha * pow_t<T>(nf, alpha - (T)1) * fK[q];
-    // psi field: -lap(psi), or W = IFFT[(K + G^2/2) psi~] when merged
-    const T lw = has_psi ? fL[q] : (T)0;
-    const T extra = sp.merged ? lw : (T)0.5 * lw;     // psi v_NL + (-lap psi)/2 when merged
-    acc[2].add(vrest * nval);
-    acc[6].add(nval);
-    // g' = psi (v_rest - mu_ref) + lap/2: near convergence mu_ref is close to
-    // mu, so the projection g = 2 scale (g' - (mu - mu_ref) psi) cancels little
-    const T gp = psit * (vrest - muref) + extra;
-    if (a.mode == 0) {
-      const T phi = fmax(psit, (T)kPhiMin);
-      const T v = vrest + extra / phi;
-      if (gout) gout[off + q] = v;
-      // residual pieces with psi = sqrt(rho), scale 1: g' = psi v_rest + lap/2
-      if (!isfinite(v)) acc[7].add((T)1);
-    } else {
-      if (gout) gout[off + q] = gp;
-      acc[3].add(gp * dq);
-      if (!isfinite(gp)) acc[7].add((T)1);
-    }
-    acc[4].add(gp * gp);
-    acc[5].add(gp * psit);
-  }
+  for (int q = threadIdx.x; q < tot; q += blockDim.x)
+    ep.point(a, pin[q], a.mode != 0 ? pd[q] : (T)0, fH ? fH[q] : (T)0, fK ? fK[q] : (T)0, fL ? fL[q] : (T)0,
+             off + q, acc);
   typename TreeVal<T>::type* scr = reinterpret_cast<typename TreeVal<T>::type*>(smem_raw);
   block_sum_tree_raw<8, T>(acc, a.partials + (size_t)blockIdx.x * 8, scr);
   if (arrive_last(a.counter)) {

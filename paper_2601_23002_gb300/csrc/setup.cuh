@@ -575,7 +575,7 @@ namespace ofdft {
 // partial[block][2] = (sum n T p, sum n (v_xc - e_xc)) over the grid.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pressure_r(const T* __restrict__ rho, size_t N, T cy, T Te, int terms,
-                                                    double* __restrict__ partial) {
+                                                    double* __restrict__ partial, int fd64, double cy_d) {
   __shared__ typename TreeVal<T>::type scr[2 * 257];
   Acc<T> acc[2];
   const T nmin = (T)kNmin;
@@ -583,9 +583,15 @@ __global__ void __launch_bounds__(256) k_pressure_r(const T* __restrict__ rho, s
     const T nval = rho[q];
     const T nf = fmax(nval, nmin);
     if (terms & 1) {
-      T eta, p;
-      fd_eta_p(nf * cy, eta, p);
-      acc[0].add(nf * Te * p);
+      if (sizeof(T) == 4 && fd64) {          // FP64 inversion, as in the evaluation
+        double eta, p;
+        fd_eta_p((double)nf * cy_d, eta, p);
+        acc[0].add((T)((double)nf * (double)Te * p));
+      } else {
+        T eta, p;
+        fd_eta_p(nf * cy, eta, p);
+        acc[0].add(nf * Te * p);
+      }
     }
     if (terms & 8) {
       T exc, vxc;
