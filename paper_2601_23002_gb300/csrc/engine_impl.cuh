@@ -94,6 +94,8 @@ class Engine : public IEngine {
   // n = 256, FP32, tiled path: the z passes with register transforms (zpass256.cuh)
   bool z256 = false, z256_allowed = true;
   size_t smem_zf256 = 0, smem_zi256 = 0;
+  // and the y and x/G-space passes of that grid (16-column tiles)
+  static constexpr int kGridY256 = 256 * 9, kGridX256 = 256 * 129 / 16;
   int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_stream = 0, nsm = 152;
   // device memory
   std::vector<void*> allocs;
@@ -585,6 +587,9 @@ class Engine : public IEngine {
     if ((rc = raise((const void*)k_zinv_epi<T>, smem_zi))) return rc;
     if (z256 && (rc = raise((const void*)k_zfwd256<T>, smem_zf256))) return rc;
     if (z256 && (rc = raise((const void*)k_zinv256<T>, smem_zi256))) return rc;
+    if (z256 && (rc = raise((const void*)k_ypass256<T, -1>, y256_bytes<T>()))) return rc;
+    if (z256 && (rc = raise((const void*)k_ypass256<T, 1>, y256_bytes<T>()))) return rc;
+    if (z256 && (rc = raise((const void*)k_xgspace256<T>, x256_bytes<T>()))) return rc;
     if ((rc = raise((const void*)k_ypass<T, -1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
@@ -756,6 +761,13 @@ class Engine : public IEngine {
       if (planes) {
         OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), plane_kern<<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
         g_rows = nh * sp.nact;
+      } else if (z256) {
+        const double yb = 2.0 * sp.nact * NH * sizeof(C);
+        const double xb = yb + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0);
+        OFDFT_RUN("k_ypass256", st, yb, k_ypass256<T, -1><<<dim3(kGridY256, sp.nact), kThreads, y256_bytes<T>(), st>>>(sp, tw_n));
+        OFDFT_RUN("k_xgspace256", st, xb, k_xgspace256<T><<<dim3(kGridX256, sp.nact), kThreads, x256_bytes<T>(), st>>>(sp, ga, tw_n));
+        OFDFT_RUN("k_ypass256", st, yb, k_ypass256<T, 1><<<dim3(kGridY256, sp.nact), kThreads, y256_bytes<T>(), st>>>(sp, tw_n));
+        g_rows = kGridX256 * sp.nact;
       } else {
         OFDFT_RUN("k_ypass", st, 2.0 * sp.nact * NH * sizeof(C), k_ypass<T, -1><<<dim3(grid_y1, sp.nact), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
         OFDFT_RUN("k_xgspace", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), k_xgspace<T><<<dim3(grid_x, sp.nact), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
@@ -764,7 +776,7 @@ class Engine : public IEngine {
       }
     }
     // epilogue partials after room for 3 fields of G-space rows
-    TV* pe = pt + (size_t)std::max(grid_x, nh) * 3 * 4;
+    TV* pe = pt + (size_t)std::max(z256 ? kGridX256 : grid_x, nh) * 3 * 4;
     if (mode == 0) mu_ref = 0.0;
     FinArgs<T> fa{pt, g_rows, pe, grid_z, res_d};
     const double cy = 9.8696044010893586188344909998762 / (1.4142135623730950488016887242097 * std::pow(Te, 1.5));
@@ -800,12 +812,16 @@ class Engine : public IEngine {
       OFDFT_RUN("k_plane_prec2", st, fb, prec2_kern<<<dim3(2 * nh), kPlaneThreads, smem_pl2, st>>>(sp, ga, pn, rev_d, tw_n));
     } else if (planes) {
       OFDFT_RUN("k_plane", st, fb, plane_kern<<<dim3(nh, 1), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
+    } else if (z256) {
+      OFDFT_RUN("k_ypass256", st, fb, k_ypass256<T, -1><<<dim3(kGridY256, 1), kThreads, y256_bytes<T>(), st>>>(sp, tw_n));
+      OFDFT_RUN("k_xgspace256", st, fb, k_xgspace256<T><<<dim3(kGridX256, 1), kThreads, x256_bytes<T>(), st>>>(sp, ga, tw_n));
+      OFDFT_RUN("k_ypass256", st, fb, k_ypass256<T, 1><<<dim3(kGridY256, 1), kThreads, y256_bytes<T>(), st>>>(sp, tw_n));
     } else {
       OFDFT_RUN("k_ypass", st, fb, k_ypass<T, -1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
       OFDFT_RUN("k_xgspace", st, fb, k_xgspace<T><<<dim3(grid_x, 1), kThreads, smem_x, st>>>(sp, ga, pn, tw_n, n, xJ));
       OFDFT_RUN("k_ypass", st, fb, k_ypass<T, 1><<<dim3(grid_y1, 1), kThreads, smem_y, st>>>(sp, pn, tw_n, n, yJ));
     }
-    TV* pe = pt + (size_t)std::max(grid_x, nh) * 3 * 4;
+    TV* pe = pt + (size_t)std::max(z256 ? kGridX256 : grid_x, nh) * 3 * 4;
     FinArgs<T> fa{pt, 0, pe, 0, res_d};
     EpiArgs<T> ea{3, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)Te, (T)1, (T)0, cs.terms, out, pe, fa,
                   counters + 0, pold, pyout};

@@ -1,5 +1,6 @@
-// The z passes of the 256^3 grid (FP32 plans on the tiled path) with the
-// half-length transforms held in registers.
+// The passes of the 256^3 grid (FP32 plans on the tiled path) with their
+// transforms held in registers: the z passes below, and after them the y pass
+// and the x pass with the G-space terms.
 //
 // A row's real-to-complex transform along z is a complex transform of half
 // length H = 128 (the even/odd packing of the generic k_zfwd / k_zinv_epi),
@@ -260,6 +261,209 @@ __global__ void __launch_bounds__(256, 2) k_zinv256(Spectra<T> sp, EpiArgs<T> a,
     finalize_eval<T>(a.fin, scr);
     if (threadIdx.x == 0) *a.counter = 0u;
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// The y and x passes for n = 256: length-256 complex transforms of the
+// columns of a 256 x 16 tile, 256 = 16 x 16, one team of 16 threads (a half
+// warp) per column: thread j holds the 16 elements j + 16 s and applies a
+// radix-16 butterfly, the team exchanges through shared memory, and thread j
+// finishes butterfly j of the second stage with the twiddles W_256^(j r).
+// The tile is staged in shared memory with a row pitch of 17 (coalesced
+// loads and stores of its 16-column rows); after the first stage the tile's
+// space holds the 16 teams' exchange buffers.
+struct Y256 {
+  static constexpr int N = 256, NH = 129, J = 16, P = J + 1, A = 16;
+  static constexpr int TEAMS = 16;                     // 256 threads / 16
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t y256_bytes() {
+  return (size_t)Y256::N * Y256::P * sizeof(cplx<T>) + (size_t)Y256::N * sizeof(cplx<T>);
+}
+template <typename T>
+__host__ __device__ constexpr size_t x256_bytes() {
+  return 2 * (size_t)Y256::N * Y256::P * sizeof(cplx<T>) + (size_t)Y256::N * sizeof(cplx<T>);
+}
+
+// v[s] = column c's elements j + 16 s of the tile (pitch 17)
+template <typename T>
+__device__ __forceinline__ void t256_load(const cplx<T>* tile, int c, int j, cplx<T> (&v)[16]) {
+#pragma unroll
+  for (int s = 0; s < 16; ++s) v[s] = tile[(j + 16 * s) * Y256::P + c];
+}
+
+// The rest of a team's transform after the radix-16 butterflies of stage 1
+// on v (element order as loaded): exchange through xb (this team's 272
+// slots; the caller has ordered any earlier use of them), stage 2 with the
+// twiddles W_256^(j r) (conjugated for DIR > 0).  On return v[r] holds the
+// result's element j + 16 r.
+// The team is one half warp: its barrier names only its own 16 lanes (the
+// other half's team may be idle).
+__device__ __forceinline__ unsigned half_warp_mask() { return 0xFFFFu << (threadIdx.x & 16); }
+
+template <typename T, int DIR>
+__device__ __forceinline__ void t256_stage2(cplx<T>* xb, const cplx<T>* __restrict__ tw, int j, cplx<T> (&v)[16]) {
+#pragma unroll
+  for (int s = 0; s < 16; ++s) xb[j * 17 + s] = v[s];              // y[16 j + s] at 17 j + s
+  __syncwarp(half_warp_mask());
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = xb[j + 17 * r];              // y[j + 16 r]
+#pragma unroll
+  for (int r = 1; r < 16; ++r) {
+    cplx<T> w = tw[j * r];
+    if (DIR > 0) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  Codelet<cplx<T>, 16, DIR>::run(v);
+}
+
+// 2./4. FFT along y for n = 256, in place.  grid.x = 256 x-rows x 9 kz tiles
+// of 16 (the last holds kz = 128 only), grid.y = active field.
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256, 3) k_ypass256(Spectra<T> sp, const cplx<T>* __restrict__ tw_n) {
+  constexpr int N = Y256::N, NH = Y256::NH, J = Y256::J, P = Y256::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tw = tile + N * P;
+  constexpr int ntz = (NH + J - 1) / J;
+  const int x = blockIdx.x / ntz, kz0 = (blockIdx.x % ntz) * J;
+  const int jn = min(J, NH - kz0);
+  cplx<T>* base = sp.s[sp.idx[blockIdx.y]] + (size_t)x * N * NH + kz0;
+  for (int q = threadIdx.x; q < N * J; q += blockDim.x) {
+    const int y = q >> 4, c = q & 15;
+    if (c < jn) cp_async_c(tile + y * P + c, base + y * NH + c, true);
+  }
+  cp_async_commit();
+  tw[threadIdx.x] = tw_n[threadIdx.x];
+  cp_async_wait<0>();
+  __syncthreads();
+  const int c = threadIdx.x >> 4, j = threadIdx.x & 15;
+  const bool act = c < jn;
+  cplx<T> v[16];
+  if (act) {
+    t256_load<T>(tile, c, j, v);
+    Codelet<cplx<T>, 16, DIR>::run(v);
+  }
+  __syncthreads();                                     // the tile becomes exchange space
+  if (act) t256_stage2<T, DIR>(tile + c * 272, tw, j, v);
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) tile[(j + 16 * r) * P + c] = v[r];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < N * J; q += blockDim.x) {
+    const int y = q >> 4, c2 = q & 15;
+    if (c2 < jn) base[y * NH + c2] = tile[y * P + c2];
+  }
+}
+
+// 3. FFT along x, the G-space terms, inverse FFT along x for n = 256.  Tile:
+// the 256 kx of 16 consecutive flattened (ky, kz) columns; grid.x = 256 * 129
+// / 16 tiles, grid.y = active field.  The forward result of thread j (kx =
+// j + 16 r) is exactly the set the inverse's first stage needs, so the
+// inverse starts in registers.  Same G-space arithmetic as k_xgspace.
+// smem: tile[256][17] | vtile[256][17] (V_loc, field 0) | tw[256].
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_xgspace256(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
+  constexpr int N = Y256::N, NH = Y256::NH, J = Y256::J, P = Y256::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* vtile = tile + N * P;
+  cplx<T>* tw = vtile + N * P;
+  constexpr size_t plane = (size_t)N * NH;             // stride between consecutive kx
+  const size_t j0 = (size_t)blockIdx.x * J;            // N * NH is a multiple of 16
+  const int fid = sp.idx[blockIdx.y];
+  const bool with_loc = fid == 0 && g.vloc != nullptr;
+  const T tp2 = g.tp2, invN = g.invN, Om = g.Om, halfOm = g.halfOm, fourpi = (T)(4.0 * kPi);
+  const T g2cut = g.g2cut_loc;
+  cplx<T>* base = sp.s[fid] + j0;
+  for (int q = threadIdx.x; q < N * J; q += blockDim.x) {
+    const int kx = q >> 4, jc = q & 15;
+    cp_async_c(tile + kx * P + jc, base + kx * plane + jc, true);
+    if (with_loc) {
+      const int jl = (int)j0 + jc;
+      const int ky = jl / NH, kz = jl - ky * NH;
+      const int mx = kx <= 127 ? kx : kx - N, my = ky <= 127 ? ky : ky - N;
+      const bool need = tp2 * (T)(mx * mx + my * my + kz * kz) <= g2cut;
+      cp_async_c(vtile + kx * P + jc, g.vloc + (need ? kx * plane + j0 + jc : 0), need);
+    }
+  }
+  cp_async_commit();
+  tw[threadIdx.x] = tw_n[threadIdx.x];
+  cp_async_wait<0>();
+  __syncthreads();
+  const int c = threadIdx.x >> 4, j = threadIdx.x & 15;
+  cplx<T> v[16];
+  t256_load<T>(tile, c, j, v);
+  Codelet<cplx<T>, 16, -1>::run(v);
+  __syncthreads();                                     // the tile becomes exchange space
+  cplx<T>* xb = tile + c * 272;
+  t256_stage2<T, -1>(xb, tw, j, v);                    // v[r] = F(kx = j + 16 r)
+  // G-space terms of column (ky, kz)
+  const int jl = (int)j0 + c;
+  const int ky = jl / NH, kz = jl - ky * NH;
+  const int my = ky <= 127 ? ky : ky - N;
+  const T w = (kz == 0 || kz == 128) ? (T)1 : (T)2;
+  AccShort<T> acc[4];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int kx = j + 16 * r;
+    const int mx = kx <= 127 ? kx : kx - N;
+    const int m2 = mx * mx + my * my + kz * kz;
+    const T G2 = tp2 * (T)m2;
+    const T vr = v[r].x * invN, vi = v[r].y * invN;    // f~(G)
+    const T a2 = vr * vr + vi * vi;
+    cplx<T> o;
+    if (fid == 0) {
+      T orr = 0, oi = 0;
+      if (g.hartree && m2 > 0) {
+        const T cc = fourpi / G2;
+        acc[0].add(w * halfOm * cc * a2);
+        orr = cc * vr; oi = cc * vi;
+      }
+      if (with_loc && G2 <= g2cut) {
+        const cplx<T> vl = vtile[kx * P + c];
+        acc[1].add(w * Om * (vr * vl.x + vi * vl.y));
+        orr += vl.x; oi += vl.y;
+      }
+      o = mk<T>(orr, oi);
+    } else if (fid == 1) {
+      const T k = g.K[m2];
+      acc[2].add(w * Om * k * a2);
+      o = mk<T>(k * vr, k * vi);
+    } else if (g.prec != nullptr) {
+      const T pg = g.prec[m2];
+      o = mk<T>(pg * vr, pg * vi);
+    } else {
+      acc[3].add(w * halfOm * G2 * a2);
+      if (sp.merged) {
+        const T k = g.K[m2];
+        acc[2].add(w * Om * k * a2);
+        const T cc = k + (T)0.5 * G2;
+        o = mk<T>(cc * vr, cc * vi);
+      } else {
+        o = mk<T>(G2 * vr, G2 * vi);
+      }
+    }
+    v[r] = o;
+  }
+  // inverse along kx: stage 1 on the elements j + 16 r already held
+  Codelet<cplx<T>, 16, +1>::run(v);
+  __syncwarp(half_warp_mask());                        // the team's reads of xb are done
+  t256_stage2<T, +1>(xb, tw, j, v);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[(j + 16 * r) * P + c] = v[r];
+  __syncthreads();
+  for (int q = threadIdx.x; q < N * J; q += blockDim.x) {
+    const int kx = q >> 4, jc = q & 15;
+    base[kx * plane + jc] = tile[kx * P + jc];
+  }
+  const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  block_sum_tree_raw<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
 }
 
 }  // namespace ofdft

@@ -552,11 +552,12 @@ def test_fp32_plan_with_fp64_fermi_dirac_inversion():
     assert err["fp32"][0] < 1e-6 and err["fp32"][1] < 1e-5
 
 
-def test_register_z_passes_at_256_match_the_generic_ones(monkeypatch):
-    # 256^3 FP32 runs its z passes with register transforms (k_zfwd256,
-    # k_zinv256); OFDFT_Z256=0 selects the generic shared-memory passes.  The
-    # butterflies, twiddles and their order are the same, so one evaluation
-    # and a short minimisation give the same bits
+def test_register_passes_at_256_match_the_generic_ones(monkeypatch):
+    # 256^3 FP32 runs its z, y and x/G-space passes with register transforms
+    # (k_zfwd256, k_zinv256, k_ypass256, k_xgspace256); OFDFT_Z256=0 selects
+    # the generic shared-memory passes.  The butterflies, twiddles and their
+    # order are the same, so the potential has the same bits; the G-space
+    # energies are summed in another order (rounding only)
     cell = config_cell(4)
     nbar = cell.n_electrons / cell.volume
     rng = np.random.default_rng(9)
@@ -569,9 +570,13 @@ def test_register_z_passes_at_256_match_the_generic_ones(monkeypatch):
         v = torch.empty_like(rho)
         e = plan.energy_potential(rho, v)
         r2 = torch.empty_like(rho)
-        m = plan.minimize(r2, start_uniform=True, max_iter=6)
+        m = plan.minimize(r2, start_uniform=True)
         plan.close()
-        out.append((e, v.cpu(), m["F_total"], r2.cpu()))
+        assert m["converged"], m
+        out.append((e, v.cpu(), m["F_total"], r2.double().cpu().numpy()))
     (e1, v1, f1, n1), (e2, v2, f2, n2) = out
-    assert e1 == e2 and torch.equal(v1, v2)
-    assert f1 == f2 and torch.equal(n1, n2)
+    assert torch.equal(v1, v2)
+    for k in e1:
+        assert abs(e1[k] - e2[k]) <= 1e-12 * max(1.0, abs(e2[k])), (k, e1[k], e2[k])
+    assert abs(f1 - f2) / cell.n_ion < 1e-8
+    assert np.linalg.norm(n1 - n2) / np.linalg.norm(n2) < 1e-5
