@@ -712,7 +712,11 @@ class Engine : public IEngine {
     const int sch = std::max(1, std::min(64, (int)(36864 / ((size_t)nh * sizeof(C)))));
     const size_t ssm = (size_t)sch * nh * sizeof(C) + (size_t)kStructRows * sch * sizeof(C) + (size_t)sch * sizeof(T);
     const int sgrid = (nrows + kStructRows - 1) / kStructRows;
-    OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, SZg, partials));
+    // one ion species (every workload here): S_Z = Z S, so the kernel sums S only
+    bool uni = true;
+    for (double z : cs.Z) uni = uni && z == cs.Z[0];
+    if (uni) OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T, true><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, SZg, partials));
+    else OFDFT_RUN("k_struct", st, (double)NH * sizeof(C) * (full ? 2 : 1), k_struct<T, false><<<sgrid, 32 * kStructRows, ssm, st>>>(phases, Z_d, nion, n, L, sf_tab, g2rows, full, mlim, sch, Sg, vloc, SZg, partials));
     int rc;
     if ((rc = sum_partials(sgrid, 1, 0, st))) return rc;
     const double rcut = 6.3 / eta;
@@ -1260,7 +1264,7 @@ int Engine<T>::build_shells(int n_shells, cudaStream_t st) {
   const int ns = (int)shell_m2.size();
   if (ns < n_shells) { set_error("grid has fewer distinct shells than requested"); return OFDFT_ERR_INVALID; }
   const int m2max = shell_m2.back();
-  if ((2.0 * kPi / L) * (2.0 * kPi / L) * m2max > std::max(156.0 / (cs.rc * cs.rc), (2.0 * kPi / L) * (2.0 * kPi / L) * 600.0)) {
+  if ((2.0 * kPi / L) * (2.0 * kPi / L) * m2max > std::max(g2cut_loc, (2.0 * kPi / L) * (2.0 * kPi / L) * 600.0)) {
     set_error("requested shells extend beyond the stored structure factor");
     return OFDFT_ERR_INVALID;
   }

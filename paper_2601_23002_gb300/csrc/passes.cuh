@@ -643,6 +643,11 @@ template <typename T> struct EpiPoint {
       vrest += vxc;
       acc[1].add(nval * exc);
     }
+    finish(a, psit, nval, nf, dq, vrest, hv, kv, lv, at, acc);
+  }
+  // the nonlocal and G-space contributions, the output and the sums
+  __device__ __forceinline__ void finish(const EpiArgs<T>& a, T psit, T nval, T nf, T dq, T vrest, T hv, T kv,
+                                         T lv, size_t at, AccShort<T> (&acc)[8]) const {
     if (has_n) vrest += hv;
     if (has_na) vrest += (T)2 * alpha * pow_t<T>(nf, alpha - (T)1) * kv;
     // psi field: -lap(psi), or W = IFFT[(K + G^2/2) psi~] when merged

@@ -44,7 +44,8 @@ static __global__ void k_phases(const double* __restrict__ pos, int n_ion, int n
 constexpr int kStructRows = 8;
 constexpr int kStructMaxKJ = 9;     // kz per lane: nh <= 32 * 9
 
-template <typename T>
+// UNI: every ion has the charge Z[0]; S_Z is then Z[0] S and is not summed.
+template <typename T, bool UNI>
 __global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __restrict__ ph,
                                                              const double* __restrict__ Z, int n_ion, int n,
                                                              double L, const double2* __restrict__ sf_tab,
@@ -118,11 +119,16 @@ __global__ void __launch_bounds__(32 * kStructRows) k_struct(const double2* __re
             const cplx<T> w = e[kz];
             const T pr = xy.x * w.x - xy.y * w.y, pi = xy.x * w.y + xy.y * w.x;
             sr[j] += pr; si[j] += pi;
-            zr[j] += zc * pr; zi[j] += zc * pi;
+            if constexpr (!UNI) { zr[j] += zc * pr; zi[j] += zc * pi; }
           }
         }
       }
     }
+  }
+  if constexpr (UNI) {
+    const T z0 = (T)Z[0];
+#pragma unroll
+    for (int j = 0; j < kStructMaxKJ; ++j) { zr[j] = z0 * sr[j]; zi[j] = z0 * si[j]; }
   }
   double ew = 0;
   if (valid) {

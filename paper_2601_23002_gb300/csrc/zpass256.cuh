@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256, 2) k_zfwd256(ProArgs<T> a, Spectra<T> sp,
 // smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | stg[nact][R][NH] | pin[2][R][N].
 // A row's real output overwrites its own staging row (pitch 2 NH reals).
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_zinv256(Spectra<T> sp, EpiArgs<T> a, const cplx<T>* __restrict__ tw_h,
+__global__ void __launch_bounds__(256, 3) k_zinv256(Spectra<T> sp, EpiArgs<T> a, const cplx<T>* __restrict__ tw_h,
                                                    const cplx<T>* __restrict__ tw_n, int R) {
   constexpr int N = Z256::N, H = Z256::H, NH = Z256::NH, A = Z256::A, B = Z256::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
