@@ -434,7 +434,8 @@ def run_serving(args, dev):
     """Poisson request stream (8-512 ions, 32^3-160^3): the plain sequential
     service rate on a sample of the stream first (every 10th request, at most
     200), then the continuous-batching server on the whole stream at 0.5, 0.9
-    and 1.5 times that rate."""
+    and 1.5 times that rate, and with every request waiting at the start
+    (the server's capacity)."""
     import numpy as np
     from paper_2601_23002_gb300.serving import Server, run_sequential, summarize
     from workloads import serving_requests
@@ -452,7 +453,12 @@ def run_serving(args, dev):
         arrivals = np.cumsum(rng.exponential(1.0 / (rho_f * mu), size=len(cells)))
         done = srv.run(arrivals, cells)
         out[f"load_{rho_f}"] = summarize(done, srv.wall)
+    # at a load of rho x the sequential rate the server can serve at most rho x
+    # that rate; its capacity shows with every request waiting at the start
+    done = srv.run(np.zeros(len(cells)), cells)
+    out["load_saturated"] = summarize(done, srv.wall)
     out["served_over_sequential_at_1.5"] = out["load_1.5"]["snapshots_per_s"] / mu
+    out["capacity_over_sequential"] = out["load_saturated"]["snapshots_per_s"] / mu
     return out
 
 

@@ -21,6 +21,96 @@ namespace ofdft {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
+// ---------------------------------------------------------------------------
+// Block cache (see engine.h).  Device blocks are keyed by (device, size);
+// pinned host blocks by size.
+namespace {
+struct BlockCache {
+  std::mutex mu;
+  std::map<std::pair<int, size_t>, std::vector<void*>> dev;
+  std::map<int, size_t> dev_bytes;                 // cached bytes per device
+  std::map<size_t, std::vector<void*>> host;
+};
+BlockCache& cache() {
+  static BlockCache* c = new BlockCache();         // never destroyed: plans may outlive statics
+  return *c;
+}
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+}  // namespace
+
+cudaError_t cached_dev_alloc(void** p, size_t bytes) {
+  BlockCache& c = cache();
+  const int d = current_device();
+  {
+    std::lock_guard<std::mutex> lock(c.mu);
+    auto it = c.dev.find({d, bytes});
+    if (it != c.dev.end() && !it->second.empty()) {
+      *p = it->second.back();
+      it->second.pop_back();
+      c.dev_bytes[d] -= bytes;
+      return cudaSuccess;
+    }
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    // give this device's cached blocks back and try once more
+    std::vector<void*> drop;
+    {
+      std::lock_guard<std::mutex> lock(c.mu);
+      for (auto it = c.dev.begin(); it != c.dev.end(); ++it)
+        if (it->first.first == d) {
+          drop.insert(drop.end(), it->second.begin(), it->second.end());
+          it->second.clear();
+        }
+      c.dev_bytes[d] = 0;
+    }
+    for (void* q : drop) cudaFree(q);
+    e = cudaMalloc(p, bytes);
+  }
+  return e;
+}
+
+void cached_dev_release(void* p, size_t bytes) {
+  if (!p) return;
+  BlockCache& c = cache();
+  const int d = current_device();
+  {
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (c.dev_bytes[d] + bytes <= kCacheCapBytes) {
+      c.dev[{d, bytes}].push_back(p);
+      c.dev_bytes[d] += bytes;
+      return;
+    }
+  }
+  cudaFree(p);
+}
+
+cudaError_t cached_host_alloc(void** p, size_t bytes) {
+  BlockCache& c = cache();
+  {
+    std::lock_guard<std::mutex> lock(c.mu);
+    auto it = c.host.find(bytes);
+    if (it != c.host.end() && !it->second.empty()) {
+      *p = it->second.back();
+      it->second.pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaMallocHost(p, bytes);
+}
+
+void cached_host_release(void* p, size_t bytes) {
+  if (!p) return;
+  BlockCache& c = cache();
+  std::lock_guard<std::mutex> lock(c.mu);
+  c.host[bytes].push_back(p);
+}
+
 // n = product of radices from {16, 12, 10, 9, 8, 6, 5, 4, 3, 2}, fewest passes.
 bool factor_radices(int n, int* radix, int* npass) {
   static const int cand[] = {16, 12, 10, 9, 8, 6, 5, 4, 3, 2};
@@ -185,7 +275,12 @@ int ofdft_plan_create(const ofdft_cell* cell, const ofdft_opts* opts, void* stre
 
 void ofdft_plan_destroy(ofdft_plan* plan) {
   if (!plan) return;
+  // the plan's blocks go back to its own device's cache
+  int cur = 0;
+  const bool have = cudaGetDevice(&cur) == cudaSuccess;
+  if (have && cur != plan->device) cudaSetDevice(plan->device);
   delete plan->eng;
+  if (have && cur != plan->device) cudaSetDevice(cur);
   delete plan;
 }
 
@@ -196,11 +291,13 @@ int ofdft_structure_factor(ofdft_plan* plan, const double* pos, int pos_on_devic
 
 int ofdft_energy_potential(ofdft_plan* plan, const void* rho, void* v_out, ofdft_energies* e_out, void* stream) {
   if (!plan || !rho) { set_error("plan and rho must not be NULL"); return OFDFT_ERR_INVALID; }
+  if (!e_out) plan->eng->note_async(stream);        // returns without synchronising
   return plan->eng->energy_potential(rho, v_out, e_out, stream);
 }
 
 int ofdft_energy_potential_async(ofdft_plan* plan, const void* rho, void* v_out, double* e_dev, void* stream) {
   if (!plan || !rho || !e_dev) { set_error("plan, rho and e_dev must not be NULL"); return OFDFT_ERR_INVALID; }
+  plan->eng->note_async(stream);
   return plan->eng->energy_potential_async(rho, v_out, e_dev, stream);
 }
 

@@ -2,6 +2,7 @@
 // engines (engine_f32.cu, engine_f64.cu).  Not part of the public header.
 #pragma once
 #include <stddef.h>
+#include <cuda_runtime.h>
 #include <string>
 #include <vector>
 
@@ -39,9 +40,32 @@ class IEngine {
   virtual int autotune(void* stream, int* tile, double* us_per_eval) = 0;
   virtual int set_tiles(const int* tile) = 0;
   virtual long long grid_points() const = 0;
+  // streams that calls returning before their work is done (the potential
+  // without host energies, the asynchronous energies) were given; drained
+  // before the plan's memory goes back to the block cache.  Every other call
+  // synchronises its stream before returning.
+  std::vector<void*> async_streams;
+  void note_async(void* s) {
+    for (void* t : async_streams) if (t == s) return;
+    async_streams.push_back(s);
+  }
   virtual int profile_enable(int timing) = 0;
   virtual int profile_read(ofdft_kernel_stat* out, int max, int* count) = 0;
 };
+
+// Device and pinned-host blocks for plans, kept in a process-wide cache on
+// release (api.cu): cudaFree and cudaFreeHost synchronise the whole device,
+// which would stall every other stream at each plan release in the serving
+// loop.  A released block is reused by a later request of the same size on
+// the same device; the caller releases a block only after the work that used
+// it has finished.  On allocation failure the device's cached blocks are
+// freed and the allocation retried.  At most kCacheCapBytes per device are
+// kept; blocks beyond that are freed at once.
+constexpr size_t kCacheCapBytes = (size_t)16 << 30;
+cudaError_t cached_dev_alloc(void** p, size_t bytes);
+void cached_dev_release(void* p, size_t bytes);
+cudaError_t cached_host_alloc(void** p, size_t bytes);
+void cached_host_release(void* p, size_t bytes);
 
 IEngine* make_engine_f32(const CellSpec& c, int m_max);
 IEngine* make_engine_f64(const CellSpec& c, int m_max);

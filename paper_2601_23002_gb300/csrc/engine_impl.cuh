@@ -98,7 +98,7 @@ class Engine : public IEngine {
   static constexpr int kGridY256 = 256 * 9, kGridX256 = 256 * 129 / 16;
   int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_stream = 0, nsm = 152;
   // device memory
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;   // (block, bytes) from the block cache
   size_t nbytes = 0;
   C *tw_n = nullptr, *tw_h = nullptr;
   double* Kd = nullptr;
@@ -164,11 +164,10 @@ class Engine : public IEngine {
   long long* sh_idx = nullptr;
   float* sh_w = nullptr;
   double* sh_out = nullptr;
+  size_t sh_bytes[4] = {0, 0, 0, 0};
   void free_shells() {
-    if (sh_ptr) cudaFree(sh_ptr);
-    if (sh_idx) cudaFree(sh_idx);
-    if (sh_w) cudaFree(sh_w);
-    if (sh_out) cudaFree(sh_out);
+    void* p[4] = {sh_ptr, sh_idx, sh_w, sh_out};
+    for (int i = 0; i < 4; ++i) cached_dev_release(p[i], sh_bytes[i]);
     sh_ptr = nullptr; sh_idx = nullptr; sh_w = nullptr; sh_out = nullptr; sh_ns = 0;
   }
   size_t n_vloc = 0;         // half-spectrum entries with |G|^2 <= g2cut_loc
@@ -189,9 +188,16 @@ class Engine : public IEngine {
     tune.xJ = env("OFDFT_XJ");
   }
   ~Engine() override {
-    for (void* p : allocs) cudaFree(p);
+    // the blocks go back to the cache once work queued without a synchronising
+    // return has drained (a stream that no longer exists: the whole device)
+    for (void* s : async_streams)
+      if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaDeviceSynchronize();
+      }
+    for (auto& a : allocs) cached_dev_release(a.first, a.second);
     free_shells();
-    if (res_h) cudaFreeHost(res_h);
+    cached_host_release(res_h, kResSlots * sizeof(double));
   }
   size_t bytes() const override { return nbytes; }
   int profile_enable(int timing) override { prof.reset(timing != 0); return OFDFT_OK; }
@@ -215,14 +221,15 @@ class Engine : public IEngine {
   template <typename P> int alloc(P** p, size_t count) {
     void* q = nullptr;
     const size_t b = count * sizeof(P);
-    cudaError_t e = cudaMalloc(&q, b > 0 ? b : 16);
+    const size_t bb = b > 0 ? (b + 255) / 256 * 256 : 256;   // sizes in 256-byte steps, for reuse
+    cudaError_t e = cached_dev_alloc(&q, bb);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error(std::string("device allocation of ") + std::to_string(b) + " bytes failed: " +
                 cudaGetErrorString(e));
       return OFDFT_ERR_OOM;
     }
-    allocs.push_back(q);
+    allocs.push_back({q, bb});
     nbytes += b;
     *p = reinterpret_cast<P*>(q);
     return OFDFT_OK;
@@ -441,7 +448,7 @@ class Engine : public IEngine {
     if ((rc = alloc(&counters, 8))) return rc;
     OFDFT_CK(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned int), st));
     OFDFT_CK(cudaMemsetAsync(res_d, 0, kResSlots * sizeof(double), st));
-    OFDFT_CK(cudaMallocHost(&res_h, kResSlots * sizeof(double)));
+    OFDFT_CK(cached_host_alloc((void**)&res_h, kResSlots * sizeof(double)));
     if ((rc = alloc(&pos_d, (size_t)cs.Z.size() * 3))) return rc;
     if ((rc = alloc(&Z_d, cs.Z.size()))) return rc;
     if ((rc = alloc(&phases, (size_t)cs.Z.size() * 3 * n))) return rc;
@@ -1293,10 +1300,14 @@ int Engine<T>::build_shells(int n_shells, cudaStream_t st) {
   }
   OFDFT_CK(cudaStreamSynchronize(st));
   free_shells();
-  OFDFT_CK(cudaMalloc((void**)&sh_ptr, ptr.size() * sizeof(int)));
-  OFDFT_CK(cudaMalloc((void**)&sh_idx, std::max<size_t>(1, idx.size()) * sizeof(long long)));
-  OFDFT_CK(cudaMalloc((void**)&sh_w, std::max<size_t>(1, wts.size()) * sizeof(float)));
-  OFDFT_CK(cudaMalloc((void**)&sh_out, 3 * (size_t)ns * sizeof(double)));
+  sh_bytes[0] = ptr.size() * sizeof(int);
+  sh_bytes[1] = std::max<size_t>(1, idx.size()) * sizeof(long long);
+  sh_bytes[2] = std::max<size_t>(1, wts.size()) * sizeof(float);
+  sh_bytes[3] = 3 * (size_t)ns * sizeof(double);
+  OFDFT_CK(cached_dev_alloc((void**)&sh_ptr, sh_bytes[0]));
+  OFDFT_CK(cached_dev_alloc((void**)&sh_idx, sh_bytes[1]));
+  OFDFT_CK(cached_dev_alloc((void**)&sh_w, sh_bytes[2]));
+  OFDFT_CK(cached_dev_alloc((void**)&sh_out, sh_bytes[3]));
   OFDFT_CK(cudaMemcpyAsync(sh_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   OFDFT_CK(cudaMemcpyAsync(sh_idx, idx.data(), idx.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
   OFDFT_CK(cudaMemcpyAsync(sh_w, wts.data(), wts.size() * sizeof(float), cudaMemcpyHostToDevice, st));

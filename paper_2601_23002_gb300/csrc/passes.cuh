@@ -535,30 +535,31 @@ static __device__ void finalize_eval(const FinArgs<T>& f, typename TreeVal<T>::t
 #pragma unroll
   for (int q = 0; q < 12; ++q) acc[q] = V{};
   const int nt = blockDim.x;
-  // a thread's next rows' loads are in flight together, added in row order
-  for (int b0 = threadIdx.x; b0 < f.ng; b0 += 4 * nt) {
-    V x[4][4];
+  // a thread's next rows' loads (32 values) are in flight together, added in
+  // row order; this one block's pass over all partials is the kernel's tail
+  for (int b0 = threadIdx.x; b0 < f.ng; b0 += 8 * nt) {
+    V x[8][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int b = b0 + u * nt;
 #pragma unroll
       for (int q = 0; q < 4; ++q) x[u][q] = b < f.ng ? __ldcg(f.pg + (size_t)b * 4 + q) : V{};
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = tree_add(acc[q], x[u][q]);
   }
-  for (int b0 = threadIdx.x; b0 < f.ne; b0 += 2 * nt) {
-    V x[2][8];
+  for (int b0 = threadIdx.x; b0 < f.ne; b0 += 4 * nt) {
+    V x[4][8];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < 4; ++u) {
       const int b = b0 + u * nt;
 #pragma unroll
       for (int q = 0; q < 8; ++q) x[u][q] = b < f.ne ? __ldcg(f.pe + (size_t)b * 8 + q) : V{};
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[4 + q] = tree_add(acc[4 + q], x[u][q]);
   }

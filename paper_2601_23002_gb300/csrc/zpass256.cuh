@@ -80,7 +80,7 @@ __device__ __forceinline__ void z256_pass2(const cplx<T>* __restrict__ xb, const
 // Forward z pass for n = 256 (prologue + real-to-complex along z), tiled
 // layout.  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | psit[R][N] | dbuf[R][N].
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_zfwd256(ProArgs<T> a, Spectra<T> sp, const cplx<T>* __restrict__ tw_h,
+__global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp, const cplx<T>* __restrict__ tw_h,
                                                    const cplx<T>* __restrict__ tw_n, int R) {
   constexpr int N = Z256::N, H = Z256::H, NH = Z256::NH, A = Z256::A, B = Z256::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256, 3) k_ypass256(Spectra<T> sp, const cplx<T
 // inverse starts in registers.  Same G-space arithmetic as k_xgspace.
 // smem: tile[256][17] | vtile[256][17] (V_loc, field 0) | tw[256].
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_xgspace256(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
+__global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
   constexpr int N = Y256::N, NH = Y256::NH, J = Y256::J, P = Y256::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
