@@ -511,7 +511,13 @@ class Engine : public IEngine {
       OFDFT_CK(cudaMemcpyAsync(precT, ph_.data(), nm2 * sizeof(T), cudaMemcpyHostToDevice, st));
       OFDFT_CK(cudaStreamSynchronize(st));
     }
-    g2cut_loc = 156.0 / (cs.rc * cs.rc);
+    // |G|^2 range of the G-space sums that fall off as Gaussians in |G| (the
+    // local pseudopotential exp(-G^2 rc^2/4), the Ewald reciprocal terms):
+    // below e^-39 = 1e-17 of their G = 0 size in FP64 plans, below e^-20.8 =
+    // 1e-9 in FP32 plans, each far under its precision's rounding.  V_loc,
+    // E_loc, the forces' G list and the structure factor's rows use it; the
+    // Ewald splitting (ewald_eta) does not depend on the precision.
+    g2cut_loc = (sizeof(T) == 4 ? 4.0 * 20.8 : 4.0 * 39.0) / (cs.rc * cs.rc);
     {
       // structure-factor tables by m^2 (FP64, host): v~(G)/Omega per unit charge
       // (-4 pi exp(-G^2 rc^2/4)/G^2, pi rc^2 at G = 0) and the Ewald reciprocal
@@ -551,12 +557,17 @@ class Engine : public IEngine {
 
   long long grid_points() const override { return (long long)N; }
 
-  // Ewald splitting: reciprocal weights exp(-G^2/(4 eta^2)) below 1e-17 at g2max
+  // |G|^2 range of the structure factor's rows and the Ewald reciprocal sum
   double ewald_g2max() const {
     const double gnyq = kPi * n / L;
     return std::min(g2cut_loc, gnyq * gnyq);
   }
-  double ewald_eta() const { return std::sqrt(ewald_g2max() / (4.0 * 39.0)); }
+  // Ewald splitting: reciprocal weights exp(-G^2/(4 eta^2)) at e^-39 at the
+  // FP64 range (or the grid's Nyquist |G|), for both precisions
+  double ewald_eta() const {
+    const double gnyq = kPi * n / L;
+    return std::sqrt(std::min(156.0 / (cs.rc * cs.rc), gnyq * gnyq) / (4.0 * 39.0));
+  }
 
   bool tiles_fit(int r, int j) const {
     const size_t lim = 227 * 1024;

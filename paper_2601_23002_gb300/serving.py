@@ -41,6 +41,39 @@ class Request:
         return self.finished - self.arrival
 
 
+def solve(cell, precision, tol, autotune=True, stream=None, device="cuda"):
+    """One request: plan, structure factor, minimisation from the uniform
+    density, plan freed.  An FP32 minimisation that stops above the
+    tolerances (its line search lost in FP32 rounding, as on small cold
+    cells close to the 1e-4 Ha residual) is finished by an FP64 plan started
+    from the FP32 density; the result says so (`finished_fp64`).
+    Returns (result, density)."""
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plan = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=precision, stream=stream)
+    try:
+        plan.structure_factor(cell.pos)
+        if autotune:
+            plan.autotune()
+        rho = torch.empty(cell.n ** 3, dtype=dt, device=device)
+        out = plan.minimize(rho, start_uniform=True, tol_F_per_ion=tol[0], tol_residual=tol[1])
+    finally:
+        plan.close()
+    out["finished_fp64"] = False
+    if precision == "fp32" and not out["converged"]:
+        p64 = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision="fp64", stream=stream)
+        try:
+            p64.structure_factor(cell.pos)
+            r64 = rho.double()
+            o64 = p64.minimize(r64, start_uniform=False, tol_F_per_ion=tol[0], tol_residual=tol[1])
+        finally:
+            p64.close()
+        o64["evaluations"] += out["evaluations"]
+        o64["iterations"] += out["iterations"]
+        o64["finished_fp64"] = True
+        out, rho = o64, r64
+    return out, rho
+
+
 class Server:
     def __init__(self, slots: int = 8, precision: str = "fp32", reserve_bytes: int = 4 << 30,
                  tol_F_per_ion: float = 1e-6, tol_residual: float = 1e-4, keep_density: bool = False,
@@ -63,23 +96,14 @@ class Server:
         return Plan.plan_bytes(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=self.precision)
 
     def _serve_one(self, req: Request, stream) -> None:
-        cell = req.cell
-        dt = torch.float32 if self.precision == "fp32" else torch.float64
         with torch.cuda.stream(stream):
-            plan = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=self.precision, stream=stream)
-            try:
-                plan.structure_factor(cell.pos)
-                if self.autotune:
-                    plan.autotune()
-                rho = torch.empty(cell.n ** 3, dtype=dt, device=torch.device("cuda", self.device))
-                out = plan.minimize(rho, start_uniform=True, tol_F_per_ion=self.tol[0], tol_residual=self.tol[1])
-                if self.keep_density:
-                    req.density = rho.double().cpu().numpy()
-                else:
-                    stream.synchronize()
-                req.result = out
-            finally:
-                plan.close()
+            out, rho = solve(req.cell, self.precision, self.tol, self.autotune, stream,
+                             torch.device("cuda", self.device))
+            if self.keep_density:
+                req.density = rho.double().cpu().numpy()
+            else:
+                stream.synchronize()
+            req.result = out
 
     def _slot_stream(self):
         torch.cuda.set_device(self.device)
@@ -175,6 +199,7 @@ def summarize(done: list[Request], wall: float) -> dict:
     lat = np.array([r.latency for r in done if not r.error])
     ok = [r for r in done if not r.error and r.result.get("converged")]
     return {"requests": len(done), "converged": len(ok), "errors": sum(1 for r in done if r.error),
+            "finished_fp64": sum(1 for r in done if r.result.get("finished_fp64")),
             "snapshots_per_s": len(ok) / wall if wall > 0 else 0.0,
             "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
@@ -185,19 +210,12 @@ def run_sequential(cells, precision: str = "fp32", tol_F_per_ion: float = 1e-6, 
                    keep_density: bool = False, autotune: bool = True):
     """The plain single-instance path: one request after another on one stream.
     Returns (results, seconds)."""
-    dt = torch.float32 if precision == "fp32" else torch.float64
     out = []
     t0 = time.perf_counter()
     for cell in cells:
-        plan = Plan(cell.L, cell.n, cell.Z, cell.T, rc=cell.rc, precision=precision)
-        plan.structure_factor(cell.pos)
-        if autotune:
-            plan.autotune()
-        rho = torch.empty(cell.n ** 3, dtype=dt, device="cuda")
-        r = plan.minimize(rho, start_uniform=True, tol_F_per_ion=tol_F_per_ion, tol_residual=tol_residual)
+        r, rho = solve(cell, precision, (tol_F_per_ion, tol_residual), autotune)
         if keep_density:
             r["density"] = rho.double().cpu().numpy()
         torch.cuda.synchronize()
-        plan.close()
         out.append(r)
     return out, time.perf_counter() - t0
