@@ -94,6 +94,9 @@ class Engine : public IEngine {
   // n = 256, FP32, tiled path: the z passes with register transforms (zpass256.cuh)
   bool z256 = false, z256_allowed = true;
   size_t smem_zf256 = 0, smem_zi256 = 0;
+  // and the cluster plane pass of that grid (spectra in plane layout;
+  // OFDFT_P256=0 keeps the tiled register passes)
+  bool p256 = false, p256_allowed = true;
   // and the y and x/G-space passes of that grid (16-column tiles)
   static constexpr int kGridY256 = 256 * 9, kGridX256 = 256 * 129 / 16;
   int grid_z = 0, grid_y1 = 0, grid_x = 0, grid_vec = 0, grid_stream = 0, nsm = 152;
@@ -182,6 +185,8 @@ class Engine : public IEngine {
     plane_allowed = !(pe && pe[0] == '0');
     const char* z2 = std::getenv("OFDFT_Z256");
     z256_allowed = !(z2 && z2[0] == '0');
+    const char* q2 = std::getenv("OFDFT_P256");
+    p256_allowed = !(q2 && q2[0] == '0');
     const char* p2 = std::getenv("OFDFT_PREC2");
     prec2_allowed = !(p2 && p2[0] == '0');
     tune.yJ = env("OFDFT_YJ");
@@ -246,7 +251,7 @@ class Engine : public IEngine {
     Spectra<T> s{};
     s.nact = 0;
     s.merged = merged() ? 1 : 0;
-    s.planes = planes ? 1 : 0;
+    s.planes = (planes || p256) ? 1 : 0;
     const bool on[3] = {use_n(), use_na() && !merged(), use_psi()};
     for (int f = 0; f < 3; ++f) {
       s.s[f] = on[f] ? spec[f] : nullptr;
@@ -304,6 +309,7 @@ class Engine : public IEngine {
     planes = plane_allowed && smem_pl <= (size_t)225 * 1024;
     // (rows per block even and dividing n^2: 8, 16 or 32)
     z256 = z256_allowed && sizeof(T) == 4 && n == 256 && !planes && (zR == 8 || zR == 16 || zR == 32);
+    p256 = z256 && p256_possible();
     smem_zf256 = z256_fwd_bytes<T>(zR);
     smem_zi256 = std::max(z256_inv_bytes<T>(zR, spectra().nact), tree_scratch_bytes<T>(12, kThreads));
     // clusters only for large grids: below n = 112 the snapshots that are
@@ -320,11 +326,21 @@ class Engine : public IEngine {
     grid_stream = (int)std::min<size_t>((size_t)nsm, (Nv / StreamCfg<T>::K + kStreamThreads - 1) / kStreamThreads);
   }
 
+  // the cluster plane pass at 256^3 for some row count (V_loc in its order is
+  // then kept whatever the tiles)
+  bool p256_possible() const { return z256_allowed && p256_allowed && sizeof(T) == 4 && n == 256 && !planes; }
+
+  // the cluster plane pass over nf fields
+  int launch_p256(const Spectra<T>& sp, const GArgs<T>& ga, int nf, double bytes, cudaStream_t st) {
+    OFDFT_RUN("k_plane256cl", st, bytes, k_plane256cl<T><<<dim3(P256::CL * nh, nf), P256::THREADS, p256_bytes<T>(), st>>>(sp, ga, tw_n));
+    return OFDFT_OK;
+  }
+
   size_t plan_bytes_estimate() {
     geometry();
     size_t b = 0;
     b += 3 * NH * sizeof(C) + 2 * NH * sizeof(C);           // spectra, vloc, S
-    if (planes) b += NH * sizeof(C);                         // vloc in plane order
+    if (planes || p256_possible()) b += NH * sizeof(C);      // vloc in plane order
     b += (6 + 3 * (size_t)m_max) * ((Nv * sizeof(T) + 255) / 256 * 256);   // psi d g gp, P g x2, history s y P y
     b += (size_t)(3 * (n / 2) * (n / 2) + 1) * (sizeof(double) + sizeof(T));
     b += (size_t)(n + h) * sizeof(C);
@@ -409,6 +425,7 @@ class Engine : public IEngine {
       OFDFT_CK(cudaMemcpyAsync(rev_d, rev.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
       if (planes && (rc = alloc(&vloc_pl, NH))) return rc;
     }
+    if (p256_possible() && (rc = alloc(&vloc_pl, NH))) return rc;
     {
       // the minimiser's 6 + 3 m vectors in one allocation (slices on
       // 256-byte boundaries): one cudaMalloc instead of thirty per plan
@@ -608,6 +625,7 @@ class Engine : public IEngine {
     if (z256 && (rc = raise((const void*)k_ypass256<T, -1>, y256_bytes<T>()))) return rc;
     if (z256 && (rc = raise((const void*)k_ypass256<T, 1>, y256_bytes<T>()))) return rc;
     if (z256 && (rc = raise((const void*)k_xgspace256<T>, x256_bytes<T>()))) return rc;
+    if (p256 && (rc = raise((const void*)k_plane256cl<T>, p256_bytes<T>()))) return rc;
     if ((rc = raise((const void*)k_ypass<T, -1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
@@ -752,6 +770,8 @@ class Engine : public IEngine {
     E_ion = res_h[0] + res_h[1] - eta / std::sqrt(kPi) * zz - kPi * Ne * Ne / (2.0 * Omega * eta * eta);
     if (planes)
       OFDFT_RUN("k_vloc_planes", st, 2.0 * NH * sizeof(C), k_vloc_planes<T><<<4 * nsm, 256, 0, st>>>(vloc, vloc_pl, rev_d, n));
+    if (p256_possible())
+      OFDFT_RUN("k_vloc_planes256", st, 2.0 * NH * sizeof(C), k_vloc_planes256<T><<<4 * nsm, 256, 0, st>>>(vloc, vloc_pl));
     if (S_out) OFDFT_CK(cudaMemcpyAsync(S_out, Sg, NH * sizeof(C), cudaMemcpyDeviceToDevice, st));
     OFDFT_CK(cudaStreamSynchronize(st));
     ions_set = true;
@@ -772,7 +792,7 @@ class Engine : public IEngine {
     const double tp = 2.0 * kPi / L;
     using TV = typename TreeVal<T>::type;          // 8 bytes, like the double slots of partials
     TV* pt = reinterpret_cast<TV*>(partials);
-    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? (planes ? vloc_pl : vloc) : nullptr, Kt, (T)(tp * tp), (T)Omega,
+    GArgs<T> ga{(cs.terms & OFDFT_TERM_LOC) ? ((planes || p256) ? vloc_pl : vloc) : nullptr, Kt, (T)(tp * tp), (T)Omega,
                 (T)(0.5 * Omega), (T)(1.0 / (double)N), (T)g2cut_loc, (cs.terms & OFDFT_TERM_HARTREE) ? 1 : 0,
                 pt};
     int g_rows = 0;                       // rows of G-space partials [g_rows][4]
@@ -783,6 +803,10 @@ class Engine : public IEngine {
       if (planes) {
         OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), plane_kern<<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
         g_rows = nh * sp.nact;
+      } else if (p256) {
+        const double pb = 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0);
+        if (int rc = launch_p256(sp, ga, sp.nact, pb, st)) return rc;
+        g_rows = P256::CL * nh * sp.nact;
       } else if (z256) {
         const double yb = 2.0 * sp.nact * NH * sizeof(C);
         const double xb = yb + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0);
@@ -819,7 +843,7 @@ class Engine : public IEngine {
   // plain vector with the G-space factor p(m^2) (GArgs::prec, EpiArgs mode 3)
   int precondition(const T* in, T* out, cudaStream_t st, const T* pold = nullptr, T* pyout = nullptr) {
     Spectra<T> sp{};
-    sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = (planes || prec2) ? 1 : 0;
+    sp.s[2] = spec[2]; sp.nact = 1; sp.idx[0] = 2; sp.merged = 0; sp.planes = (planes || prec2 || p256) ? 1 : 0;
     ProArgs<T> pa{1, nullptr, in, nullptr, (T)0, (T)1, (T)cs.alpha, (T)0};
     const double tp = 2.0 * kPi / L;
     using TV = typename TreeVal<T>::type;
@@ -834,6 +858,8 @@ class Engine : public IEngine {
       OFDFT_RUN("k_plane_prec2", st, fb, prec2_kern<<<dim3(2 * nh), kPlaneThreads, smem_pl2, st>>>(sp, ga, pn, rev_d, tw_n));
     } else if (planes) {
       OFDFT_RUN("k_plane", st, fb, plane_kern<<<dim3(nh, 1), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
+    } else if (p256) {
+      if (int rc = launch_p256(sp, ga, 1, fb, st)) return rc;
     } else if (z256) {
       OFDFT_RUN("k_ypass256", st, fb, k_ypass256<T, -1><<<dim3(kGridY256, 1), kThreads, y256_bytes<T>(), st>>>(sp, tw_n));
       OFDFT_RUN("k_xgspace256", st, fb, k_xgspace256<T><<<dim3(kGridX256, 1), kThreads, x256_bytes<T>(), st>>>(sp, ga, tw_n));

@@ -19,6 +19,7 @@
 // unnormalised inverse), so results agree with the generic path to FP32
 // rounding; the parity tests run both against the oracle.
 #pragma once
+#include <cooperative_groups.h>
 #include "passes.cuh"
 
 namespace ofdft {
@@ -77,8 +78,8 @@ __device__ __forceinline__ void z256_pass2(const cplx<T>* __restrict__ xb, const
   }
 }
 
-// Forward z pass for n = 256 (prologue + real-to-complex along z), tiled
-// layout.  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | psit[R][N] | dbuf[R][N].
+// Forward z pass for n = 256 (prologue + real-to-complex along z), tiled or
+// plane layout (Spectra::planes).  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | psit[R][N] | dbuf[R][N].
 template <typename T>
 __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp, const cplx<T>* __restrict__ tw_h,
                                                    const cplx<T>* __restrict__ tw_n, int R) {
@@ -152,8 +153,11 @@ __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp,
     }
     __syncwarp();
     if (act) {
-      // X[k] = (Z[k] + Z*[H-k])/2 - (i/2) W_N^k (Z[k] - Z*[H-k]), k = 0..H (Z[H] = Z[0])
-      cplx<T>* out = sp.s[fid] + (row0 + r) * NH;
+      // X[k] = (Z[k] + Z*[H-k])/2 - (i/2) W_N^k (Z[k] - Z*[H-k]), k = 0..H (Z[H] = Z[0]);
+      // plane layout: entry (k, row) at k N^2 + row (the four teams of a
+      // warp, consecutive rows, fill whole 32-byte sectors)
+      cplx<T>* out = sp.planes ? sp.s[fid] + row0 + r : sp.s[fid] + (row0 + r) * NH;
+      const size_t kstride = sp.planes ? (size_t)N * N : 1;
 #pragma unroll
       for (int s = 0; s <= A; ++s) {
         const int k = j + B * s;
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp,
         const cplx<T> zc = cconj(xb[Z256::xpos(k == 0 ? 0 : H - k)]);
         const cplx<T> e = cadd(zk, zc);
         const cplx<T> wo = cmul(twN[k], csub(zk, zc));
-        out[k] = mk<T>((T)0.5 * (e.x + wo.y), (T)0.5 * (e.y - wo.x));
+        out[k * kstride] = mk<T>((T)0.5 * (e.x + wo.y), (T)0.5 * (e.y - wo.x));
       }
     }
     __syncwarp();                                      // xb is rewritten by the next round
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp,
 }
 
 // Inverse z pass for n = 256 (complex-to-real along z) fused with the
-// pointwise functional, tiled layout.
+// pointwise functional, tiled or plane layout.
 // smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | stg[nact][R][NH] | pin[2][R][N].
 // A row's real output overwrites its own staging row (pitch 2 NH reals).
 template <typename T>
@@ -185,9 +189,21 @@ __global__ void __launch_bounds__(256, 3) k_zinv256(Spectra<T> sp, EpiArgs<T> a,
   T* pin = reinterpret_cast<T*>(stg + (size_t)sp.nact * R * NH);
   const size_t row0 = (size_t)blockIdx.x * R;
   const size_t off = row0 * N;
-  // spectra rows (contiguous per field: R NH complex, 16-byte aligned since R is even)
-  for (int f = 0; f < sp.nact; ++f)
-    cp_async_block16(stg + (size_t)f * R * NH, sp.s[sp.idx[f]] + row0 * NH, (size_t)R * NH * sizeof(cplx<T>));
+  // spectra rows: tiled layout, contiguous per field (R NH complex, 16-byte
+  // aligned since R is even); plane layout, runs of R rows per kz
+  for (int f = 0; f < sp.nact; ++f) {
+    if (sp.planes) {
+      const cplx<T>* src = sp.s[sp.idx[f]] + row0;
+      cplx<T>* dst = stg + (size_t)f * R * NH;
+      const int lgR = __ffs(R) - 1;
+      for (int q = threadIdx.x; q < R * NH; q += blockDim.x) {
+        const int k = q >> lgR, r = q & (R - 1);
+        cp_async_c(dst + r * NH + k, src + (size_t)k * N * N + r, true);
+      }
+    } else {
+      cp_async_block16(stg + (size_t)f * R * NH, sp.s[sp.idx[f]] + row0 * NH, (size_t)R * NH * sizeof(cplx<T>));
+    }
+  }
   {
     const T* src0 = a.mode == 0 ? a.rho : (a.mode == 3 ? a.pold : a.psi);
     if (a.mode != 3 || a.pyout) cp_async_block16(pin, src0 + off, (size_t)R * N * sizeof(T));
@@ -319,6 +335,49 @@ __device__ __forceinline__ void t256_stage2(cplx<T>* xb, const cplx<T>* __restri
   Codelet<cplx<T>, 16, DIR>::run(v);
 }
 
+// The G-space terms at one wave vector (m^2 = |m|^2, Hermitian weight w) of
+// field fid's transform F (unnormalised): the output spectrum and the energy
+// sums acc (0 E_H, 1 E_loc, 2 E_NL, 3 E_vW raw), as in k_xgspace.  vloc()
+// returns V_loc(G) where |G|^2 <= the cutoff (called only there).
+template <typename T, typename VL>
+__device__ __forceinline__ cplx<T> gspace_point(int fid, const GArgs<T>& g, int merged, bool with_loc, int m2, T w,
+                                                cplx<T> F, VL&& vloc, AccShort<T> (&acc)[4]) {
+  const T G2 = g.tp2 * (T)m2;
+  const T vr = F.x * g.invN, vi = F.y * g.invN;        // f~(G)
+  const T a2 = vr * vr + vi * vi;
+  if (fid == 0) {
+    T orr = 0, oi = 0;
+    if (g.hartree && m2 > 0) {
+      const T cc = (T)(4.0 * kPi) / G2;
+      acc[0].add(w * g.halfOm * cc * a2);
+      orr = cc * vr; oi = cc * vi;
+    }
+    if (with_loc && G2 <= g.g2cut_loc) {
+      const cplx<T> vl = vloc();
+      acc[1].add(w * g.Om * (vr * vl.x + vi * vl.y));
+      orr += vl.x; oi += vl.y;
+    }
+    return mk<T>(orr, oi);
+  }
+  if (fid == 1) {
+    const T k = g.K[m2];
+    acc[2].add(w * g.Om * k * a2);
+    return mk<T>(k * vr, k * vi);
+  }
+  if (g.prec != nullptr) {
+    const T pg = g.prec[m2];
+    return mk<T>(pg * vr, pg * vi);
+  }
+  acc[3].add(w * g.halfOm * G2 * a2);
+  if (merged) {
+    const T k = g.K[m2];
+    acc[2].add(w * g.Om * k * a2);
+    const T cc = k + (T)0.5 * G2;
+    return mk<T>(cc * vr, cc * vi);
+  }
+  return mk<T>(G2 * vr, G2 * vi);
+}
+
 // 2./4. FFT along y for n = 256, in place.  grid.x = 256 x-rows x 9 kz tiles
 // of 16 (the last holds kz = 128 only), grid.y = active field.
 template <typename T, int DIR>
@@ -377,7 +436,7 @@ __global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g
   const size_t j0 = (size_t)blockIdx.x * J;            // N * NH is a multiple of 16
   const int fid = sp.idx[blockIdx.y];
   const bool with_loc = fid == 0 && g.vloc != nullptr;
-  const T tp2 = g.tp2, invN = g.invN, Om = g.Om, halfOm = g.halfOm, fourpi = (T)(4.0 * kPi);
+  const T tp2 = g.tp2;
   const T g2cut = g.g2cut_loc;
   cplx<T>* base = sp.s[fid] + j0;
   for (int q = threadIdx.x; q < N * J; q += blockDim.x) {
@@ -413,42 +472,7 @@ __global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g
     const int kx = j + 16 * r;
     const int mx = kx <= 127 ? kx : kx - N;
     const int m2 = mx * mx + my * my + kz * kz;
-    const T G2 = tp2 * (T)m2;
-    const T vr = v[r].x * invN, vi = v[r].y * invN;    // f~(G)
-    const T a2 = vr * vr + vi * vi;
-    cplx<T> o;
-    if (fid == 0) {
-      T orr = 0, oi = 0;
-      if (g.hartree && m2 > 0) {
-        const T cc = fourpi / G2;
-        acc[0].add(w * halfOm * cc * a2);
-        orr = cc * vr; oi = cc * vi;
-      }
-      if (with_loc && G2 <= g2cut) {
-        const cplx<T> vl = vtile[kx * P + c];
-        acc[1].add(w * Om * (vr * vl.x + vi * vl.y));
-        orr += vl.x; oi += vl.y;
-      }
-      o = mk<T>(orr, oi);
-    } else if (fid == 1) {
-      const T k = g.K[m2];
-      acc[2].add(w * Om * k * a2);
-      o = mk<T>(k * vr, k * vi);
-    } else if (g.prec != nullptr) {
-      const T pg = g.prec[m2];
-      o = mk<T>(pg * vr, pg * vi);
-    } else {
-      acc[3].add(w * halfOm * G2 * a2);
-      if (sp.merged) {
-        const T k = g.K[m2];
-        acc[2].add(w * Om * k * a2);
-        const T cc = k + (T)0.5 * G2;
-        o = mk<T>(cc * vr, cc * vi);
-      } else {
-        o = mk<T>(G2 * vr, G2 * vi);
-      }
-    }
-    v[r] = o;
+    v[r] = gspace_point<T>(fid, g, sp.merged, with_loc, m2, w, v[r], [&]() { return vtile[kx * P + c]; }, acc);
   }
   // inverse along kx: stage 1 on the elements j + 16 r already held
   Codelet<cplx<T>, 16, +1>::run(v);
@@ -464,6 +488,194 @@ __global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g
   }
   const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
   block_sum_tree_raw<4, T>(acc, g.partials + b * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
+}
+
+// ---------------------------------------------------------------------------
+// The x-y transforms and the G-space terms of one kz plane of one field in a
+// cluster of eight blocks (plane layout, [kz][x][y]).  A 256 x 256 FP32 plane
+// (512 KB) fits no block's shared memory; block c of the cluster keeps the 32
+// rows x = 8 b + c (b = 0..31, pitch 257).  The transform along x splits as
+// 256 = 32 x 8 (four-step):
+//   X[k2 + 32 k1] = sum_c W_8^(c k1) [W_256^(c k2) sum_b W_32^(b k2) x[8 b + c]],
+// so each block does the inner 32-point transforms of its own rows, and only
+// the outer 8-point transforms (one per (k2, ky)) combine the blocks:
+//   1. forward transforms along y of its 32 rows;
+//   2. forward 32-point transforms along b of its 256 columns, times
+//      W_256^(c k2) (all local);
+//   -- cluster barrier --
+//   3. for its k2 = 4 c .. 4 c + 3 and every ky: the eight values (one per
+//      block, same offset: a warp reads 256 contiguous bytes of each) through
+//      distributed shared memory, the 8-point transform, the G-space terms at
+//      kx = k2 + 32 k1, the inverse 8-point transform, the values back;
+//   -- cluster barrier --
+//   4. times W_256^(-c k2), inverse 32-point transforms along k2; inverse
+//      transforms along y of its rows; the rows back to memory.
+// Two cluster barriers in all.  The y transforms keep the y pass's
+// butterflies exactly (half-warp teams, 256 = 16 x 16, the exchange in place
+// in the row); the x transforms group the same sums differently (32 x 8 in
+// place of 16 x 16), so results agree with the other passes to FP32 rounding.
+// grid = (8 * 129 kz, active field), 256 threads, 66 KB of shared memory
+// (slice[32][257] | tw[256]): up to three blocks per SM.
+struct P256 {
+  static constexpr int N = 256, NH = 129, CL = 8, ROWS = N / CL, P = N + 1, THREADS = 256;
+};
+
+template <typename T>
+__host__ __device__ constexpr size_t p256_bytes() {
+  return ((size_t)P256::ROWS * P256::P + P256::N) * sizeof(cplx<T>);
+}
+
+// A half-warp team's length-256 transform of one row (256 = 16 x 16, the
+// butterflies of t256_stage2), in place: the exchange between the two
+// stages goes through the row itself, element e at
+// 16 (e / 16) + (e + e / 16) % 16 (the 16 lanes hit 16 different bank pairs
+// in both exchange patterns).
+template <typename T, int DIR>
+__device__ __forceinline__ void p256_row(cplx<T>* row, const cplx<T>* __restrict__ tw, int j) {
+  const unsigned mask = half_warp_mask();
+  cplx<T> v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) v[s] = row[j + 16 * s];
+  Codelet<cplx<T>, 16, DIR>::run(v);
+  __syncwarp(mask);                                    // the team has read the row
+#pragma unroll
+  for (int s = 0; s < 16; ++s) row[16 * j + ((s + j) & 15)] = v[s];   // y[16 j + s]
+  __syncwarp(mask);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = row[16 * r + ((j + r) & 15)];   // y[j + 16 r]
+#pragma unroll
+  for (int r = 1; r < 16; ++r) {
+    cplx<T> w = tw[j * r];
+    if (DIR > 0) w.y = -w.y;
+    v[r] = cmul(v[r], w);
+  }
+  Codelet<cplx<T>, 16, DIR>::run(v);
+  __syncwarp(mask);                                    // the team has read the exchange
+#pragma unroll
+  for (int r = 0; r < 16; ++r) row[j + 16 * r] = v[r];
+}
+
+// Length-32 transform of v in registers, natural order in and out: one
+// radix-2 step (x_i +- x_(i+16), the difference times W_32^i = tw[8 i]), then
+// 16-point transforms of the two halves (even and odd outputs).
+template <typename T, int DIR>
+__device__ __forceinline__ void p256_dft32(cplx<T> (&v)[32], const cplx<T>* __restrict__ tw) {
+  cplx<T> u[16], d[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    u[i] = cadd(v[i], v[i + 16]);
+    d[i] = csub(v[i], v[i + 16]);
+    if (i > 0) {
+      cplx<T> w = tw[8 * i];
+      if (DIR > 0) w.y = -w.y;
+      d[i] = cmul(d[i], w);
+    }
+  }
+  Codelet<cplx<T>, 16, DIR>::run(u);
+  Codelet<cplx<T>, 16, DIR>::run(d);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) { v[2 * k] = u[k]; v[2 * k + 1] = d[k]; }
+}
+
+template <typename T>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(256, 3)
+k_plane256cl(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
+  namespace cg = cooperative_groups;
+  constexpr int N = P256::N, ROWS = P256::ROWS, P = P256::P, CL = P256::CL;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* slice = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tw = slice + ROWS * P;
+  const int c = (int)cl.block_rank();
+  const int kz = blockIdx.x / CL;
+  const int fid = sp.idx[blockIdx.y];
+  cplx<T>* gpl = sp.s[fid] + (size_t)kz * N * N + (size_t)c * N;   // row x = 8 b + c at gpl + 8 b N
+  for (int q = threadIdx.x; q < ROWS * N; q += blockDim.x) {
+    const int b = q >> 8, y = q & (N - 1);
+    cp_async_c(slice + b * P + y, gpl + (size_t)b * CL * N + y, true);
+  }
+  cp_async_commit();
+  tw[threadIdx.x] = tw_n[threadIdx.x];
+  cp_async_wait<0>();
+  __syncthreads();
+  const int team = threadIdx.x >> 4, j = threadIdx.x & 15, t = threadIdx.x;
+  // 1. along y
+  for (int b0 = 0; b0 < ROWS; b0 += 16) p256_row<T, -1>(slice + (b0 + team) * P, tw, j);
+  __syncthreads();
+  // 2. column ky = t: 32-point transforms along b, twiddles W_256^(c k2)
+  {
+    cplx<T> v[32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) v[b] = slice[b * P + t];
+    p256_dft32<T, -1>(v, tw);
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw[c * k2]);
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) slice[k2 * P + t] = v[k2];
+  }
+  cl.sync();
+  // 3. across the cluster: the (k2, ky = t) sums of the eight blocks
+  cplx<T>* part[CL];
+#pragma unroll
+  for (int o = 0; o < CL; ++o) part[o] = cl.map_shared_rank(slice, o);
+  const bool with_loc = fid == 0 && g.vloc != nullptr;
+  const T w = (kz == 0 || kz == N / 2) ? (T)1 : (T)2;
+  const int my = t <= 127 ? t : t - N;
+  AccShort<T> acc[4];
+  for (int i = 0; i < 4; ++i) {
+    const int k2 = 4 * c + i;
+    cplx<T> z[CL];
+#pragma unroll
+    for (int o = 0; o < CL; ++o) z[o] = part[o][k2 * P + t];
+    Codelet<cplx<T>, 8, -1>::run(z);                   // z[k1] = F(kx = k2 + 32 k1)
+    // V_loc in plane layout [kz][kx][ky]
+    const cplx<T>* vl = with_loc ? g.vloc + (size_t)kz * N * N + t : nullptr;
+#pragma unroll
+    for (int k1 = 0; k1 < CL; ++k1) {
+      const int kx = k2 + 32 * k1;
+      const int mx = kx <= 127 ? kx : kx - N;
+      const int m2 = mx * mx + my * my + kz * kz;
+      z[k1] = gspace_point<T>(fid, g, sp.merged, with_loc, m2, w, z[k1], [&]() { return vl[(size_t)kx * N]; }, acc);
+    }
+    Codelet<cplx<T>, 8, +1>::run(z);
+#pragma unroll
+    for (int o = 0; o < CL; ++o) part[o][k2 * P + t] = z[o];
+  }
+  cl.sync();                                           // (no remote access after this)
+  // 4. column ky = t: twiddles W_256^(-c k2), inverse 32-point transforms
+  {
+    cplx<T> v[32];
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) v[k2] = slice[k2 * P + t];
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], cconj(tw[c * k2]));
+    p256_dft32<T, 1>(v, tw);
+#pragma unroll
+    for (int b = 0; b < 32; ++b) slice[b * P + t] = v[b];
+  }
+  __syncthreads();
+  for (int b0 = 0; b0 < ROWS; b0 += 16) p256_row<T, 1>(slice + (b0 + team) * P, tw, j);
+  __syncthreads();
+  for (int q = threadIdx.x; q < ROWS * N; q += blockDim.x) {
+    const int b = q >> 8, y = q & (N - 1);
+    gpl[(size_t)b * CL * N + y] = slice[b * P + y];
+  }
+  const size_t bi = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  block_sum_tree_raw<4, T>(acc, g.partials + bi * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
+}
+
+// One-time reorder of V_loc from the tiled layout [kx][ky][kz] into plane
+// layout, natural order: dst[(kz 256 + kx) 256 + ky] = src[(kx 256 + ky) 129 + kz].
+template <typename T>
+__global__ void k_vloc_planes256(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst) {
+  constexpr int N = 256, NH = 129;
+  const size_t tot = (size_t)NH * N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+    const int ky = (int)(i % N);
+    const int kx = (int)((i / N) % N);
+    const int kz = (int)(i / ((size_t)N * N));
+    dst[i] = src[((size_t)kx * N + ky) * NH + kz];
+  }
 }
 
 }  // namespace ofdft
