@@ -328,12 +328,39 @@ class Engine : public IEngine {
 
   // the cluster plane pass at 256^3 for some row count (V_loc in its order is
   // then kept whatever the tiles)
+  // the z passes at 256^3 for the plan's rows per block (FP32 plans)
+  int launch_zfwd256(const ProArgs<T>& pa, const Spectra<T>& sp, double bytes, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+      auto k = zR == 8 ? k_zfwd256<T, 8> : (zR == 16 ? k_zfwd256<T, 16> : k_zfwd256<T, 32>);
+      OFDFT_RUN("k_zfwd256", st, bytes, k<<<grid_z, kThreads, smem_zf256, st>>>(pa, sp, tw_h, tw_n));
+      return OFDFT_OK;
+    } else {
+      set_error("the 256^3 register z passes are FP32 only");
+      return OFDFT_ERR_INVALID;
+    }
+  }
+  int launch_zinv256(const Spectra<T>& sp, const EpiArgs<T>& ea, double bytes, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+      auto k = zR == 8 ? k_zinv256<T, 8> : (zR == 16 ? k_zinv256<T, 16> : k_zinv256<T, 32>);
+      OFDFT_RUN("k_zinv256", st, bytes, k<<<grid_z, kThreads, smem_zi256, st>>>(sp, ea, tw_h, tw_n));
+      return OFDFT_OK;
+    } else {
+      set_error("the 256^3 register z passes are FP32 only");
+      return OFDFT_ERR_INVALID;
+    }
+  }
+
   bool p256_possible() const { return z256_allowed && p256_allowed && sizeof(T) == 4 && n == 256 && !planes; }
 
   // the cluster plane pass over nf fields
   int launch_p256(const Spectra<T>& sp, const GArgs<T>& ga, int nf, double bytes, cudaStream_t st) {
-    OFDFT_RUN("k_plane256cl", st, bytes, k_plane256cl<T><<<dim3(P256::CL * nh, nf), P256::THREADS, p256_bytes<T>(), st>>>(sp, ga, tw_n));
-    return OFDFT_OK;
+    if constexpr (sizeof(T) == 4) {
+      OFDFT_RUN("k_plane256cl", st, bytes, k_plane256cl<T><<<dim3(P256::CL * nh, nf), P256::THREADS, p256_bytes<T>(), st>>>(sp, ga, tw_n));
+      return OFDFT_OK;
+    } else {
+      set_error("the cluster plane pass is FP32 only");
+      return OFDFT_ERR_INVALID;
+    }
   }
 
   size_t plan_bytes_estimate() {
@@ -620,12 +647,19 @@ class Engine : public IEngine {
     int rc;
     if ((rc = raise((const void*)k_zfwd<T>, smem_zf))) return rc;
     if ((rc = raise((const void*)k_zinv_epi<T>, smem_zi))) return rc;
-    if (z256 && (rc = raise((const void*)k_zfwd256<T>, smem_zf256))) return rc;
-    if (z256 && (rc = raise((const void*)k_zinv256<T>, smem_zi256))) return rc;
+    if constexpr (sizeof(T) == 4) {
+      if (z256 && (rc = raise((const void*)k_zfwd256<T, 8>, z256_fwd_bytes<T>(8)))) return rc;
+      if (z256 && (rc = raise((const void*)k_zfwd256<T, 16>, z256_fwd_bytes<T>(16)))) return rc;
+      if (z256 && (rc = raise((const void*)k_zfwd256<T, 32>, z256_fwd_bytes<T>(32)))) return rc;
+      if (z256 && (rc = raise((const void*)k_zinv256<T, 8>, smem_zi256))) return rc;
+      if (z256 && (rc = raise((const void*)k_zinv256<T, 16>, smem_zi256))) return rc;
+      if (z256 && (rc = raise((const void*)k_zinv256<T, 32>, smem_zi256))) return rc;
+    }
     if (z256 && (rc = raise((const void*)k_ypass256<T, -1>, y256_bytes<T>()))) return rc;
     if (z256 && (rc = raise((const void*)k_ypass256<T, 1>, y256_bytes<T>()))) return rc;
     if (z256 && (rc = raise((const void*)k_xgspace256<T>, x256_bytes<T>()))) return rc;
-    if (p256 && (rc = raise((const void*)k_plane256cl<T>, p256_bytes<T>()))) return rc;
+    if constexpr (sizeof(T) == 4)
+      if (p256 && (rc = raise((const void*)k_plane256cl<T>, p256_bytes<T>()))) return rc;
     if ((rc = raise((const void*)k_ypass<T, -1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_ypass<T, 1>, smem_y))) return rc;
     if ((rc = raise((const void*)k_xgspace<T>, smem_x))) return rc;
@@ -798,8 +832,9 @@ class Engine : public IEngine {
     int g_rows = 0;                       // rows of G-space partials [g_rows][4]
     if (sp.nact > 0) {
       const double zb = (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (double)sp.nact * NH * sizeof(C);
-      if (z256) OFDFT_RUN("k_zfwd256", st, zb, k_zfwd256<T><<<grid_z, kThreads, smem_zf256, st>>>(pa, sp, tw_h, tw_n, zR));
-      else OFDFT_RUN("k_zfwd", st, zb, k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+      if (z256) {
+        if (int rc = launch_zfwd256(pa, sp, zb, st)) return rc;
+      } else OFDFT_RUN("k_zfwd", st, zb, k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
       if (planes) {
         OFDFT_RUN("k_plane", st, 2.0 * sp.nact * NH * sizeof(C) + ((cs.terms & OFDFT_TERM_LOC) ? (double)n_vloc * sizeof(C) : 0.0), plane_kern<<<dim3(nh, sp.nact), kPlaneThreads, smem_pl, st>>>(sp, ga, pn, rev_d, tw_n));
         g_rows = nh * sp.nact;
@@ -829,8 +864,9 @@ class Engine : public IEngine {
     EpiArgs<T> ea{mode, rho, ps, dd, (T)t, (T)scale, (T)cs.alpha, (T)Te, (T)cy, (T)mu_ref, cs.terms, out, pe, fa,
                   counters + 0, nullptr, nullptr, dsc, cs.fd64 ? 1 : 0, cy};
     const double eb = (double)sp.nact * NH * sizeof(C) + (double)(mode == 0 ? 1 : 2) * N * sizeof(T) + (out ? (double)N * sizeof(T) : 0.0);
-    if (z256) OFDFT_RUN("k_zinv256", st, eb, k_zinv256<T><<<grid_z, kThreads, smem_zi256, st>>>(sp, ea, tw_h, tw_n, zR));
-    else OFDFT_RUN("k_zinv_epi", st, eb, k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+    if (z256) {
+      if (int rc = launch_zinv256(sp, ea, eb, st)) return rc;
+    } else OFDFT_RUN("k_zinv_epi", st, eb, k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     if (sync) {
       OFDFT_CK(cudaMemcpyAsync(res_h, res_d, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
       OFDFT_CK(cudaStreamSynchronize(st));
@@ -851,8 +887,9 @@ class Engine : public IEngine {
     GArgs<T> ga{nullptr, Kt, (T)(tp * tp), (T)Omega, (T)(0.5 * Omega), (T)(1.0 / (double)N), (T)g2cut_loc, 0, pt,
                 precT};
     const double fb = 2.0 * NH * sizeof(C);
-    if (z256) OFDFT_RUN("k_zfwd256", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd256<T><<<grid_z, kThreads, smem_zf256, st>>>(pa, sp, tw_h, tw_n, zR));
-    else OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
+    if (z256) {
+      if (int rc = launch_zfwd256(pa, sp, (double)N * sizeof(T) + NH * sizeof(C), st)) return rc;
+    } else OFDFT_RUN("k_zfwd", st, (double)N * sizeof(T) + NH * sizeof(C), k_zfwd<T><<<grid_z, kThreads, smem_zf, st>>>(pa, sp, ph, tw_h, tw_n, n, zR, zP));
     if (prec2) {
       // one field: two blocks (a cluster) per kz plane
       OFDFT_RUN("k_plane_prec2", st, fb, prec2_kern<<<dim3(2 * nh), kPlaneThreads, smem_pl2, st>>>(sp, ga, pn, rev_d, tw_n));
@@ -874,8 +911,9 @@ class Engine : public IEngine {
     EpiArgs<T> ea{3, nullptr, in, in, (T)0, (T)1, (T)cs.alpha, (T)Te, (T)1, (T)0, cs.terms, out, pe, fa,
                   counters + 0, pold, pyout};
     const double pb = (double)NH * sizeof(C) + (double)N * sizeof(T) * (pyout ? 3.0 : 1.0);
-    if (z256) OFDFT_RUN("k_zinv256", st, pb, k_zinv256<T><<<grid_z, kThreads, smem_zi256, st>>>(sp, ea, tw_h, tw_n, zR));
-    else OFDFT_RUN("k_zinv_epi", st, pb, k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
+    if (z256) {
+      if (int rc = launch_zinv256(sp, ea, pb, st)) return rc;
+    } else OFDFT_RUN("k_zinv_epi", st, pb, k_zinv_epi<T><<<grid_z, kThreads, smem_zi, st>>>(sp, ea, ph, tw_h, tw_n, n, zR, zP));
     return OFDFT_OK;
   }
 

@@ -79,10 +79,11 @@ __device__ __forceinline__ void z256_pass2(const cplx<T>* __restrict__ xb, const
 }
 
 // Forward z pass for n = 256 (prologue + real-to-complex along z), tiled or
-// plane layout (Spectra::planes).  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | psit[R][N] | dbuf[R][N].
-template <typename T>
+// plane layout (Spectra::planes); R rows per block (8, 16 or 32: a template
+// parameter, so the row arithmetic is shifts and masks).  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | psit[R][N] | dbuf[R][N].
+template <typename T, int R>
 __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp, const cplx<T>* __restrict__ tw_h,
-                                                   const cplx<T>* __restrict__ tw_n, int R) {
+                                                   const cplx<T>* __restrict__ tw_n) {
   constexpr int N = Z256::N, H = Z256::H, NH = Z256::NH, A = Z256::A, B = Z256::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* twN = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -177,9 +178,9 @@ __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp,
 // pointwise functional, tiled or plane layout.
 // smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | stg[nact][R][NH] | pin[2][R][N].
 // A row's real output overwrites its own staging row (pitch 2 NH reals).
-template <typename T>
+template <typename T, int R>
 __global__ void __launch_bounds__(256, 3) k_zinv256(Spectra<T> sp, EpiArgs<T> a, const cplx<T>* __restrict__ tw_h,
-                                                   const cplx<T>* __restrict__ tw_n, int R) {
+                                                   const cplx<T>* __restrict__ tw_n) {
   constexpr int N = Z256::N, H = Z256::H, NH = Z256::NH, A = Z256::A, B = Z256::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* twN = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -195,9 +196,8 @@ __global__ void __launch_bounds__(256, 3) k_zinv256(Spectra<T> sp, EpiArgs<T> a,
     if (sp.planes) {
       const cplx<T>* src = sp.s[sp.idx[f]] + row0;
       cplx<T>* dst = stg + (size_t)f * R * NH;
-      const int lgR = __ffs(R) - 1;
       for (int q = threadIdx.x; q < R * NH; q += blockDim.x) {
-        const int k = q >> lgR, r = q & (R - 1);
+        const int k = q / R, r = q % R;
         cp_async_c(dst + r * NH + k, src + (size_t)k * N * N + r, true);
       }
     } else {
@@ -494,7 +494,9 @@ __global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g
 // The x-y transforms and the G-space terms of one kz plane of one field in a
 // cluster of eight blocks (plane layout, [kz][x][y]).  A 256 x 256 FP32 plane
 // (512 KB) fits no block's shared memory; block c of the cluster keeps the 32
-// rows x = 8 b + c (b = 0..31, pitch 257).  The transform along x splits as
+// rows x = 8 b + c (b = 0..31, unpadded: every access below has a warp's
+// lanes along a row, or at exchange slots that differ in bank).  The
+// transform along x splits as
 // 256 = 32 x 8 (four-step):
 //   X[k2 + 32 k1] = sum_c W_8^(c k1) [W_256^(c k2) sum_b W_32^(b k2) x[8 b + c]],
 // so each block does the inner 32-point transforms of its own rows, and only
@@ -515,9 +517,10 @@ __global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g
 // in the row); the x transforms group the same sums differently (32 x 8 in
 // place of 16 x 16), so results agree with the other passes to FP32 rounding.
 // grid = (8 * 129 kz, active field), 256 threads, 66 KB of shared memory
-// (slice[32][257] | tw[256]): up to three blocks per SM.
+// (slice[32][256] | tw[256]): up to three blocks per SM.  FP32 only (the
+// row copies move two complex values per 16 bytes).
 struct P256 {
-  static constexpr int N = 256, NH = 129, CL = 8, ROWS = N / CL, P = N + 1, THREADS = 256;
+  static constexpr int N = 256, NH = 129, CL = 8, ROWS = N / CL, P = N, THREADS = 256;
 };
 
 template <typename T>
@@ -580,6 +583,7 @@ __device__ __forceinline__ void p256_dft32(cplx<T> (&v)[32], const cplx<T>* __re
 template <typename T>
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(256, 3)
 k_plane256cl(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
+  static_assert(sizeof(T) == 4, "FP32 plans only");
   namespace cg = cooperative_groups;
   constexpr int N = P256::N, ROWS = P256::ROWS, P = P256::P, CL = P256::CL;
   cg::cluster_group cl = cg::this_cluster();
@@ -590,9 +594,9 @@ k_plane256cl(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
   const int kz = blockIdx.x / CL;
   const int fid = sp.idx[blockIdx.y];
   cplx<T>* gpl = sp.s[fid] + (size_t)kz * N * N + (size_t)c * N;   // row x = 8 b + c at gpl + 8 b N
-  for (int q = threadIdx.x; q < ROWS * N; q += blockDim.x) {
-    const int b = q >> 8, y = q & (N - 1);
-    cp_async_c(slice + b * P + y, gpl + (size_t)b * CL * N + y, true);
+  for (int q = threadIdx.x; q < ROWS * N / 2; q += blockDim.x) {   // 16-byte pieces
+    const int b = q >> 7, y = (q & 127) * 2;
+    cp_async<16>(slice + b * P + y, gpl + (size_t)b * CL * N + y, true);
   }
   cp_async_commit();
   tw[threadIdx.x] = tw_n[threadIdx.x];
@@ -656,9 +660,9 @@ k_plane256cl(Spectra<T> sp, GArgs<T> g, const cplx<T>* __restrict__ tw_n) {
   __syncthreads();
   for (int b0 = 0; b0 < ROWS; b0 += 16) p256_row<T, 1>(slice + (b0 + team) * P, tw, j);
   __syncthreads();
-  for (int q = threadIdx.x; q < ROWS * N; q += blockDim.x) {
-    const int b = q >> 8, y = q & (N - 1);
-    gpl[(size_t)b * CL * N + y] = slice[b * P + y];
+  for (int q = threadIdx.x; q < ROWS * N / 2; q += blockDim.x) {
+    const int b = q >> 7, y = (q & 127) * 2;
+    *reinterpret_cast<float4*>(gpl + (size_t)b * CL * N + y) = *reinterpret_cast<const float4*>(slice + b * P + y);
   }
   const size_t bi = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
   block_sum_tree_raw<4, T>(acc, g.partials + bi * 4, reinterpret_cast<typename TreeVal<T>::type*>(smem_raw));
