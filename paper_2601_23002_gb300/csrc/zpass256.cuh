@@ -40,8 +40,8 @@ __host__ __device__ constexpr size_t z256_common_bytes() {
   return ((size_t)(Z256::NH + Z256::H) * sizeof(cplx<T>) + 15) / 16 * 16 +
          (size_t)Z256::TEAMS * Z256::XP * sizeof(cplx<T>);
 }
-template <typename T> __host__ __device__ constexpr size_t z256_fwd_bytes(int R) {
-  return z256_common_bytes<T>() + 2 * (size_t)R * Z256::N * sizeof(T);
+template <typename T> __host__ __device__ constexpr size_t z256_fwd_bytes(int /*R: no row buffers*/) {
+  return z256_common_bytes<T>();
 }
 template <typename T> __host__ __device__ constexpr size_t z256_inv_bytes(int R, int nact) {
   return z256_common_bytes<T>() + (size_t)nact * R * Z256::NH * sizeof(cplx<T>);
@@ -80,34 +80,25 @@ __device__ __forceinline__ void z256_pass2(const cplx<T>* __restrict__ xb, const
 
 // Forward z pass for n = 256 (prologue + real-to-complex along z), tiled or
 // plane layout (Spectra::planes); R rows per block (8, 16 or 32: a template
-// parameter, so the row arithmetic is shifts and masks).  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP] | psit[R][N] | dbuf[R][N].
+// parameter, so the row arithmetic is shifts and masks).  Each team reads its
+// row's pairs (x_2m, x_2m+1) straight from memory (rho, or psi and d) and
+// forms the field's input in registers.  smem: twN[NH] | twH[H] | xbuf[TEAMS][XP]
+// (37 KB: four blocks per SM).
 template <typename T, int R>
-__global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp, const cplx<T>* __restrict__ tw_h,
+__global__ void __launch_bounds__(256, 4) k_zfwd256(ProArgs<T> a, Spectra<T> sp, const cplx<T>* __restrict__ tw_h,
                                                    const cplx<T>* __restrict__ tw_n) {
   constexpr int N = Z256::N, H = Z256::H, NH = Z256::NH, A = Z256::A, B = Z256::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* twN = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* twH = twN + NH;
   cplx<T>* xbuf = reinterpret_cast<cplx<T>*>(smem_raw + (((size_t)(NH + H) * sizeof(cplx<T>) + 15) / 16 * 16));
-  T* psit = reinterpret_cast<T*>(xbuf + (size_t)Z256::TEAMS * Z256::XP);
-  T* dbuf = psit + (size_t)R * N;
   const size_t row0 = (size_t)blockIdx.x * R;        // R divides N * N
   const size_t off = row0 * N;
   const T* src0 = a.mode == 0 ? a.rho : a.psi;
   const bool has_d = a.mode != 0 && a.d != nullptr;
-  cp_async_block16(psit, src0 + off, (size_t)R * N * sizeof(T));
-  if (has_d) cp_async_block16(dbuf, a.d + off, (size_t)R * N * sizeof(T));
   for (int q = threadIdx.x; q < NH + H; q += blockDim.x) twN[q] = q < NH ? tw_n[q] : tw_h[q - NH];
-  cp_async_commit();
-  cp_async_wait<0>();
   __syncthreads();
   const T tstep = a.dsc ? (T)a.dsc[2] : a.t;
-  for (int q = threadIdx.x; q < R * N; q += blockDim.x) {
-    const T x = psit[q];
-    if (a.mode == 0) { dbuf[q] = x; psit[q] = sqrt(fmax(x, (T)0)); }
-    else if (has_d) psit[q] = x + tstep * dbuf[q];
-  }
-  __syncthreads();
   const T scale = a.dsc ? (T)a.dsc[0] : a.scale, alpha = a.alpha, nmin = (T)kNmin;
   const T psi_shift = a.dsc ? (T)a.dsc[1] : a.psi_shift;
   const int team = threadIdx.x / B, j = threadIdx.x % B;
@@ -122,17 +113,27 @@ __global__ void __launch_bounds__(256, 3) k_zfwd256(ProArgs<T> a, Spectra<T> sp,
     if (act) {
       // pass 1: z_m = (x_2m, x_2m+1) at m = j + 8 s, radix 16
       cplx<T> v[A];
-      const T* pr = psit + r * N;
-      const T* dr = dbuf + r * N;
+      const float2* pr = reinterpret_cast<const float2*>(src0 + off + (size_t)r * N);
+      const float2* dr = has_d ? reinterpret_cast<const float2*>(a.d + off + (size_t)r * N) : nullptr;
+      float2 w[A];
+#pragma unroll
+      for (int s = 0; s < A; ++s) w[s] = __ldg(pr + j + B * s);
+      if (has_d) {
+#pragma unroll
+        for (int s = 0; s < A; ++s) {
+          const float2 dd = __ldg(dr + j + B * s);
+          w[s].x = w[s].x + tstep * dd.x; w[s].y = w[s].y + tstep * dd.y;
+        }
+      }
 #pragma unroll
       for (int s = 0; s < A; ++s) {
-        const int m = j + B * s;
-        T x0 = pr[2 * m], x1 = pr[2 * m + 1];
+        T x0 = w[s].x, x1 = w[s].y;
         if (fid == 2) {
+          if (a.mode == 0) { x0 = sqrt(fmax(x0, (T)0)); x1 = sqrt(fmax(x1, (T)0)); }
           x0 -= psi_shift; x1 -= psi_shift;
         } else {
           T n0, n1;
-          if (a.mode == 0) { n0 = dr[2 * m]; n1 = dr[2 * m + 1]; }
+          if (a.mode == 0) { n0 = x0; n1 = x1; }
           else { n0 = scale * x0 * x0; n1 = scale * x1 * x1; }
           if (fid == 0) { x0 = n0; x1 = n1; }
           else { x0 = pow_t<T>(fmax(n0, nmin), alpha); x1 = pow_t<T>(fmax(n1, nmin), alpha); }
