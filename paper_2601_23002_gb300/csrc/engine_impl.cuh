@@ -122,7 +122,9 @@ class Engine : public IEngine {
   bool prec2 = false, prec2_allowed = true;
   size_t smem_pl2 = 0;
   PlaneKernel<T> prec2_kern = nullptr;
-  C* vloc_pl = nullptr;      // V_loc in plane layout and position order
+  // V_loc in plane layout: position order for the plane pass, natural order
+  // [kz][kx][ky] for the 256^3 cluster plane pass
+  C* vloc_pl = nullptr;
   C* spec[3] = {nullptr, nullptr, nullptr};
   T *psi = nullptr, *d = nullptr, *g = nullptr, *gp = nullptr;
   // preconditioned two-loop recursion: P g (current and previous g), P y of

@@ -1,6 +1,8 @@
-// The passes of the 256^3 grid (FP32 plans on the tiled path) with their
-// transforms held in registers: the z passes below, and after them the y pass
-// and the x pass with the G-space terms.
+// The passes of the 256^3 grid (FP32 plans) with their transforms held in
+// registers: the z passes below; then the x-y transforms with the G-space
+// terms, either on one kz plane per cluster of eight blocks (plane layout,
+// k_plane256cl, the default) or as the y pass and the x pass on tiles (tiled
+// layout, k_ypass256 / k_xgspace256).
 //
 // A row's real-to-complex transform along z is a complex transform of half
 // length H = 128 (the even/odd packing of the generic k_zfwd / k_zinv_epi),
@@ -506,8 +508,7 @@ __global__ void __launch_bounds__(256, 3) k_xgspace256(Spectra<T> sp, GArgs<T> g
 // (512 KB) fits no block's shared memory; block c of the cluster keeps the 32
 // rows x = 8 b + c (b = 0..31, unpadded: every access below has a warp's
 // lanes along a row, or at exchange slots that differ in bank).  The
-// transform along x splits as
-// 256 = 32 x 8 (four-step):
+// transform along x splits as 256 = 32 x 8 (four-step):
 //   X[k2 + 32 k1] = sum_c W_8^(c k1) [W_256^(c k2) sum_b W_32^(b k2) x[8 b + c]],
 // so each block does the inner 32-point transforms of its own rows, and only
 // the outer 8-point transforms (one per (k2, ky)) combine the blocks:
