@@ -614,3 +614,46 @@ def test_register_passes_at_256_match_the_generic_ones(monkeypatch):
             f1, n1 = m1
             assert abs(f1 - f2) / cell.n_ion < 1e-6, env
             assert np.linalg.norm(n1 - n2) / np.linalg.norm(n2) < 5e-5, env
+
+
+def test_256_passes_with_three_fields(monkeypatch):
+    # a = 5/6: n^a is a third transformed field beside n and psi, so the
+    # 256^3 z passes take 48 row transforms per 16-row block (two rounds of
+    # their 32 teams) and the cluster plane pass three fields per launch.
+    # The three forms against each other (the register passes bit for bit
+    # with the generic ones) and against the oracle; 16 Z=3 ions, a smooth
+    # density of a few low-frequency modes.
+    n = 256
+    cell = random_cell(11, 16, 3.0, 2.5, 0.3, n)
+    nbar = cell.n_electrons / cell.volume
+    rng = np.random.default_rng(5)
+    x = np.arange(n) * (2 * np.pi / n)
+    X, Y, Zc = np.meshgrid(x, x, x, indexing="ij")
+    pert = np.zeros((n, n, n))
+    for _ in range(6):
+        m = rng.integers(-3, 4, size=3)
+        pert += rng.uniform(0.02, 0.05) * np.cos(m[0] * X + m[1] * Y + m[2] * Zc + rng.uniform(0, 2 * np.pi))
+    rho = nbar * (1.0 + pert)
+    rho *= cell.n_electrons / (rho.sum() * cell.volume / rho.size)
+    out = []
+    envs = ({}, {"OFDFT_P256": "0"}, {"OFDFT_Z256": "0"})
+    for env in envs:
+        for k in ("OFDFT_P256", "OFDFT_Z256"):
+            monkeypatch.delenv(k, raising=False)
+        for k, val in env.items():
+            monkeypatch.setenv(k, val)
+        out.append(gpu_eval(cell, rho.reshape(-1), precision="fp32", alpha=5 / 6))
+    (e1, v1), (e2, v2), (e3, v3) = out
+    assert np.array_equal(v2, v3)
+    # the n^a field keeps its mean (the psi field's is removed before its
+    # transform), so each form's FP32 rounding scales with that mean, and the
+    # two groupings of the x transform differ by more than in the two-field
+    # case (2.8e-6 of max|v| measured)
+    assert np.max(np.abs(v1 - v3)) / np.max(np.abs(v3)) < 1e-5
+    ref_e, ref_v = Functional(cell, alpha=5 / 6).evaluate(rho)
+    for e, v in ((e1, v1), (e3, v3)):
+        err_v = np.max(np.abs(v.reshape(n, n, n) - ref_v)) / np.max(np.abs(ref_v))
+        print("three fields: |dF|/ion", abs(e["F_total"] - ref_e["total"]) / cell.n_ion, "max|dv|/max|v|", err_v)
+        assert abs(e["F_total"] - ref_e["total"]) / cell.n_ion < 1e-6
+        assert abs(e["E_NL"] - ref_e["nl"]) / cell.n_ion < 1e-6
+        assert err_v < 5e-4
